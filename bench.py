@@ -1,0 +1,409 @@
+#!/usr/bin/env python3
+"""Throughput of the matrix-free stability hot path on one GB300 (or N replicas).
+
+Workload: the 2D cylinder wake at 512x256 (Re 60, dt 0.0025, sampling period
+T = 0.5, i.e. 200 linearised steps per product with M = exp(T A)), Krylov
+basis of dimension 128.  One bench "step" is one Krylov expansion step of
+the eigen-solver: the propagator product w = M v (steps a1-a5 of the path,
+200 time steps) followed by the CGS2 orthogonalisation of w against 64 basis
+vectors (step a6), both through the C ABI.  The metric is grid-point time
+steps per second of the linearised stepper (nx ny T/dt per step), whole job.
+Also reported: the FP32 stepper on the same workload, the time to the leading
+eigenvalues with Krylov-Schur (FP64 and FP32), the roofline of the dominant
+kernel measured live with CUDA events, an end-to-end number through host
+buffers, the SM clocks seen during the timed region, and the CPU oracle timed
+on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+# the CPU oracle leg runs single-threaded (numpy FFT is single-threaded; pin
+# BLAS too so that the reported core count is exact)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt-steps/s + time to leading eigs at 1e-8 (FP64) vs FP32/batched; % HBM roofline"
+UNIT = "grid-pt-steps/s"
+NX, NY = 512, 256
+RE = 60.0
+DT = 0.01 * 128 / NX          # CFL kept at the 128x64 value
+T_SAMPLE = 0.5
+KRYLOV_M = 128
+BASIS_J = KRYLOV_M // 2       # basis size the timed CGS2 runs against
+NEV = 8
+WORKLOAD = "cylinder wake 512x256, Re 60, Krylov step: M v (T=0.5, 200 linearised steps) + CGS2 vs 64 vectors"
+L2_FLUSH_BYTES = 512 << 20
+N_SMS = 152
+FP64_FLOP_PER_CLK_SM = 4      # 2 DFMA per clock per SM: the recipe's 1.25 TFLOP/s at 2.07 GHz
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--no-eigs", action="store_true", help="skip the time-to-eigenvalues legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ flop model
+
+def fft_flops(N: int) -> int:
+    """FP64 operations of one complex length-N transform as implemented:
+    radix-8 passes (56 flops per butterfly, plus 7 twiddle products of 6
+    flops after the first pass), then one radix-4 (16 + 3x6) or radix-2
+    (4 + 6) pass."""
+    logn = int(np.log2(N))
+    fl, nsl = 0, 0
+    while logn - nsl >= 3:
+        fl += (N // 8) * (56 + (42 if nsl > 0 else 0))
+        nsl += 3
+    rem = logn - nsl
+    if rem == 2:
+        fl += (N // 4) * (16 + (18 if nsl > 0 else 0))
+    elif rem == 1:
+        fl += (N // 2) * (4 + (6 if nsl > 0 else 0))
+    return fl
+
+
+def kernel_flops(nx: int, ny: int) -> dict:
+    """Algorithmic FP64 flops per launch of each step kernel (linearised step)."""
+    nh = nx // 2
+    rows_fft = (ny // 2) * fft_flops(nx)      # one complex transform per row pair
+    cols_fft = nh * fft_flops(ny)              # one complex transform per packed column
+    split = (ny // 2) * nh * 8                 # half-spectrum split / merge per pair
+    return {
+        "col_poisson": 2 * cols_fft + nh * ny * 3,
+        "row_inverse_psi": rows_fft + (ny // 2) * nh * 4,
+        "row_forward_rhs": rows_fft + split + nx * ny * 15,
+        "col_update": 3 * cols_fft + nh * ny * 14,
+        "row_inverse_star": ny * fft_flops(nx) + ny * nh * 4,
+        "row_forward_pen": rows_fft + split + nx * ny * 20,
+    }
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("stepper.cu", "fft.cuh", "common.cuh", "stepper.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1804_03859_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    if d.get("src_hash") != src_hash():
+        return None
+    return d.get("kernels", {}).get(kernel)
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------- CPU oracle
+
+def cpu_oracle_sample(nsteps_sample: int = 20, seed: int = 0):
+    """Time the oracle on a bounded sample of one bench step: nsteps_sample of
+    the 200 linearised steps of M v plus one CGS2 against BASIS_J vectors."""
+    from oracle import ns2d
+    from paper_1804_03859_gb300 import inputs
+
+    cfg = ns2d.Config(nx=NX, ny=NY, dt=DT, Re=RE)
+    base = ns2d.Base.from_omega(inputs.wake_like_field(NY, NX, seed=seed), cfg)
+    v = inputs.gaussian_field(NY, NX, seed=seed + 1)
+    V = np.linalg.qr(np.random.default_rng(seed).standard_normal((NX * NY, BASIS_J)))[0]
+    t0 = time.perf_counter()
+    w = ns2d.step_linear(v, nsteps_sample, base, cfg).ravel()
+    h = V.T @ w
+    w = w - V @ h
+    h2 = V.T @ w
+    w = w - V @ h2
+    el = time.perf_counter() - t0
+    return nsteps_sample * NX * NY, el
+
+
+# -------------------------------------------------------------- reference
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    # W warm-up and K timed samples of the oracle
+    for _ in range(args.warmup):
+        cpu_oracle_sample(5)
+    pts = 0
+    el = 0.0
+    for s in range(args.steps):
+        p, e = cpu_oracle_sample(20, seed=s)
+        pts += p
+        el += e
+    val = pts / el
+    sample = f"{args.steps} samples of 20 of the 200 linearised steps of M v plus one CGS2 vs {BASIS_J} vectors, 512x256"
+    out = {
+        "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY], "Re": RE, "dt": DT, "T": T_SAMPLE},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------- native
+
+def run_native(args, rank: int, world: int):
+    import torch
+
+    from paper_1804_03859_gb300 import build, inputs, nsstab
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build() if rank == 0 else None
+    if world > 1:
+        torch.distributed.barrier()
+    dev = torch.device("cuda", local)
+    nsteps = int(round(T_SAMPLE / DT))
+    pts_per_step = nsteps * NX * NY
+    base = torch.from_numpy(inputs.wake_like_field(NY, NX, seed=0)).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def make(prec):
+        st = nsstab.Stepper(nx=NX, ny=NY, dt=DT, Re=RE, precision=prec)
+        st.stepper_set_base(base)
+        return st
+
+    # basis of BASIS_J orthonormal vectors (FP64, column k contiguous)
+    g = torch.Generator(device="cpu").manual_seed(1234 + rank)
+    Vh = torch.linalg.qr(torch.randn(NX * NY, BASIS_J, generator=g, dtype=torch.float64))[0]
+    V = Vh.T.contiguous().to(dev)
+    v0 = torch.from_numpy(inputs.gaussian_field(NY, NX, seed=1)).to(dev)
+    w = torch.empty_like(v0)
+
+    def one_step(st, vin):
+        st.apply_expTL(None, vin, w, T_SAMPLE)
+        return nsstab.cgs2_orthogonalize(V, NX * NY, BASIS_J, w)
+
+    def timed(st, K, W):
+        for _ in range(W):
+            one_step(st, v0)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        total = 0.0
+        stream = torch.cuda.current_stream()
+        for _ in range(K):
+            flush.fill_(1.0)                                   # evict L2 between timed steps
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step(st, v0)
+            e1.record(stream)
+            e1.synchronize()
+            total += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            t = torch.tensor([total], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total / 1e3
+
+    st64 = make(64)
+    with ClockSampler(local) as clk:
+        el64 = timed(st64, args.steps, args.warmup)
+    value = world * args.steps * pts_per_step / el64
+
+    st32 = make(32)
+    el32 = timed(st32, args.steps, args.warmup)
+    value32 = world * args.steps * pts_per_step / el32
+
+    # end to end through host buffers: H2D of v, M v + CGS2, D2H of w
+    host_v = torch.from_numpy(inputs.gaussian_field(NY, NX, seed=2)).pin_memory()
+    host_w = torch.empty(NY, NX, dtype=torch.float64).pin_memory()
+    dv = torch.empty_like(v0)
+    for _ in range(args.warmup):
+        dv.copy_(host_v, non_blocking=True)
+        one_step(st64, dv)
+        host_w.copy_(w, non_blocking=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        dv.copy_(host_v, non_blocking=True)
+        one_step(st64, dv)
+        host_w.copy_(w, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    e2e = {"value": world * args.steps * pts_per_step / e2e_el, "unit": UNIT,
+           "h2d_bytes_per_step": host_v.numel() * 8, "d2h_bytes_per_step": host_w.numel() * 8 + (BASIS_J + 1) * 8}
+
+    # live per-kernel times of the FP64 stepper (CUDA events on its stream)
+    prof_steps = nsteps
+    ms = st64.stepper_profile_linear(v0, prof_steps)
+    dom = max(ms, key=ms.get)
+    fl = kernel_flops(NX, NY)
+    dur = ms[dom] / prof_steps / 1e3
+    sm_max = peaks().get("sm_max_mhz", 2070.0) or 2070.0
+    peak64 = N_SMS * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+    achieved = fl[dom] / dur / 1e12
+    tr = load_traffic(dom)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s", "frac": achieved / peak64,
+                "traffic": tr, "kernel": dom, "kernel_ms": ms[dom] / prof_steps,
+                "flops_per_launch": fl[dom],
+                "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x max SM clock (profiling recipe's 1.25 TFLOP/s)",
+                "share": {k: v / sum(ms.values()) for k, v in ms.items()}}
+    ms32 = st32.stepper_profile_linear(v0, prof_steps)
+    step_flops = sum(fl.values())
+
+    # time to the leading eigenvalues (Krylov-Schur, m = 128, nev = 8)
+    eigs = None
+    if not args.no_eigs:
+        eigs = {}
+        ref_mu = None
+        for prec, st, tol in ((64, st64, 1e-8), (32, st32, 1e-5)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = st.arnoldi_eigs(None, v0, m=KRYLOV_M, nev=NEV, tol=tol, T=T_SAMPLE, max_restarts=4)
+            el = time.perf_counter() - t0
+            d = {"seconds": el, "n_matvec": r.n_matvec, "n_conv": r.n_conv, "n_eig": len(r.mu), "tol": tol,
+                 "leading_mu": [r.mu[0].real, r.mu[0].imag]}
+            if prec == 64:
+                ref_mu = r.mu
+            elif ref_mu is not None:
+                errs = [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in r.mu]
+                d["rel_err_vs_fp64"] = errs
+            eigs[f"fp{prec}"] = d
+
+    if rank != 0:
+        return
+    clocks = clk.summary()
+    cpu = None
+    if not args.no_cpu:
+        pts, el = cpu_oracle_sample(20)
+        cpu = {"value": pts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "20 of the 200 linearised steps of one M v plus one CGS2 vs 64 vectors at 512x256, "
+                         "numpy FP64 on one host core"}
+    per_step_launches = 1 + 6 * nsteps + 8
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * el64 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [NX, NY], "Re": RE, "dt": DT, "T": T_SAMPLE,
+                   "steps_per_matvec": nsteps, "krylov_m": KRYLOV_M, "cgs2_basis": BASIS_J,
+                   "base_flow": "synthetic developed-wake field (not a converged steady state)",
+                   "l2": "flushed (512 MiB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * per_step_launches,
+        "clocks": clocks,
+        "fp32": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * el32 / args.steps,
+                 "kernel_ms": {k: v / prof_steps for k, v in ms32.items()}},
+        "step_flops_fp64": step_flops,
+        "step_tflops_fp64": step_flops * nsteps / (el64 / args.steps) / 1e12,
+        "time_to_eigs": eigs,
+    }
+    print(json.dumps(out))
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_native(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

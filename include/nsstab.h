@@ -1,0 +1,188 @@
+/*
+ * nsstab.h - C ABI of the GB300-native matrix-free stability library.
+ *
+ * The library implements the data-parallel hot path of the time-stepper
+ * approach to hydrodynamic stability (Loiseau, Bucci, Cherubini, Robinet,
+ * "Time-stepping and Krylov methods for large-scale instability problems"):
+ *   - a 2D incompressible Navier-Stokes time-stepper in vorticity-
+ *     streamfunction form that applies the nonlinear map G (Sec. 2, Eq. 2;
+ *     Sec. 3.1.2, Eq. 41) and the exponential propagator
+ *     M v = exp(T A) v of the linearised equations (Sec. 3, Eqs. 29-30;
+ *     Sec. 3.1.2, Eq. 42; Sec. 3.2, Eq. 55);
+ *   - the Arnoldi factorisation (Sec. 3.2.1, Algorithm 1, Eq. 57) with
+ *     CGS2 orthogonalisation and the Krylov-Schur restart (Sec. 3.2.2,
+ *     Eqs. 60-63) that consume M;
+ *   - selective frequency damping (Sec. 3.1.1, Eq. 40) for the base flow.
+ *
+ * Conventions for every entry point:
+ *   - Fields are float64, row-major [ny][nx] (x fastest), contiguous, in
+ *     DEVICE memory owned by the caller, unless an argument says "host".
+ *   - All device work is enqueued on the stream given to stepper_create
+ *     (a cudaStream_t passed as void*; NULL = legacy default stream).
+ *   - Return value: NSSTAB_OK (0) on success, a negative NSSTAB_ERR_* code
+ *     on failure (nothing is guaranteed about outputs then), a positive
+ *     soft status (NSSTAB_NOT_CONVERGED, NSSTAB_DIVERGED) when the call ran
+ *     to completion but did not meet its target.  nsstab_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - Calls marked "asynchronous" only enqueue work: results are valid
+ *     after the stream is synchronised.  All other calls synchronise the
+ *     stream before returning.
+ *   - A stepper is not thread-safe: one host thread at a time per stepper.
+ *
+ * Grid: nx, ny powers of two in [8, 4096]; x_i = i Lx/nx, y_j = j Ly/ny; the
+ * box is doubly periodic.
+ */
+#ifndef NSSTAB_H
+#define NSSTAB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NSSTAB_OK 0
+#define NSSTAB_NOT_CONVERGED 1      /* target not met within the budget */
+#define NSSTAB_DIVERGED 2           /* non-finite values appeared */
+#define NSSTAB_ERR_INVALID_ARG (-1)
+#define NSSTAB_ERR_CUDA (-2)
+#define NSSTAB_ERR_OUT_OF_MEMORY (-3)
+#define NSSTAB_ERR_NUMERICAL (-4)   /* dense eigen-solver failed */
+
+/* Physical and numerical parameters of one stepper.  See
+ * nsstab_config_default for the 128x64 cylinder-wake values. */
+typedef struct nsstab_config {
+    int nx, ny;             /* grid points in x and y (powers of two)          */
+    double Lx, Ly;          /* box size (16, 8)                                 */
+    double dt;              /* time step                                        */
+    double Re;              /* Reynolds number; viscosity nu = 1/Re             */
+    double Uinf;            /* free-stream velocity along x (1)                 */
+    double cyl_x, cyl_y;    /* cylinder centre (4, 4)                           */
+    double cyl_D;           /* cylinder diameter (1); <= 0 disables it          */
+    double eta;             /* Brinkman permeability (1e-3)                     */
+    double mask_cells;      /* width of the smoothed mask edge in x-cells (2)   */
+    double sponge_frac;     /* fringe occupies x >= (1 - frac) Lx (0.1)         */
+    double sponge_sigma;    /* peak fringe strength (10); <= 0 disables it      */
+    int precision;          /* 64: FP64 stepper; 32: FP32 stepper (FP64 I/O)    */
+} nsstab_config;
+
+typedef struct nsstab_stepper nsstab_stepper;   /* opaque */
+
+/* Fill *cfg with the 128x64 cylinder defaults (Re 50, dt 0.01, FP64). */
+void nsstab_config_default(nsstab_config* cfg);
+
+/* Create a stepper for cfg; it allocates and owns its device workspace
+ * (about 13 fields of nx*ny values of the stepper's precision).
+ * stream: cudaStream_t (as void*) on which all of this stepper's work runs.
+ * Errors: INVALID_ARG (bad sizes or parameters), OUT_OF_MEMORY, CUDA. */
+int stepper_create(const nsstab_config* cfg, void* stream, nsstab_stepper** out);
+
+/* Release the stepper and its device memory (synchronises its stream). */
+void stepper_destroy(nsstab_stepper* st);
+
+/* Step a1 alone: psi with 5-point Laplacian(psi) = -omega (mean removed),
+ * solved in Fourier space.  omega, psi: device [ny][nx].  Asynchronous. */
+int stepper_poisson(nsstab_stepper* st, const double* omega, double* psi);
+
+/* March the nonlinear equations (Sec. 3, Eq. 28) nsteps steps of a1-a4:
+ * omega <- G^nsteps(omega).  AB1 on the first step, AB2 after.  omega:
+ * device [ny][nx], in/out.  Asynchronous. */
+int step_nonlinear(nsstab_stepper* st, double* omega, int nsteps);
+
+/* Set the frozen base flow (vorticity Omega_b, device [ny][nx]) used by the
+ * linearised stepper.  The stepper keeps its own copy.  Asynchronous. */
+int stepper_set_base(nsstab_stepper* st, const double* base_omega);
+
+/* M v = exp(T A) v (Eq. 42 / Eq. 55): T/dt linearised steps about the base
+ * flow, AB1 start, so M is a fixed linear map of v.  base_omega: device
+ * [ny][nx] (it is then also kept as the stepper's base), or NULL to use the
+ * base of the last stepper_set_base.  v_in, v_out: device [ny][nx]; they
+ * may alias.  T must be a whole number of steps.  Asynchronous. */
+int apply_expTL(nsstab_stepper* st, const double* base_omega,
+                const double* v_in, double* v_out, double T);
+
+/* Base-flow residual r(q) = ||G_1(q) - q||_h / dt with G_1 one AB1 step
+ * and ||f||_h = sqrt(sum f^2 dx dy) (fixed point of Eq. 32).  q: device.
+ * *r: host.  Synchronous. */
+int stepper_residual(nsstab_stepper* st, const double* q, double* r);
+
+/* Selective frequency damping (Sec. 3.1.1, Eq. 40): march
+ *   X* = G(X^n),  X^{n+1} = X* - dt chi (X* - Y^n),
+ *   Y^{n+1} = Y^n + dt (X* - Y^n) / Delta,   Y^0 = X^0,
+ * evaluating r(X) every check_every steps, until r <= tol or max_steps.
+ * omega: device [ny][nx], in: X^0, out: last X.  *residual, *steps: host.
+ * Returns NSSTAB_OK, NSSTAB_NOT_CONVERGED or NSSTAB_DIVERGED.  Synchronous. */
+int sfd_baseflow(nsstab_stepper* st, double* omega, double chi, double Delta,
+                 double tol, long max_steps, int check_every,
+                 double* residual, long* steps);
+
+/* Leading eigenvalues of M = exp(T A) about base_omega (Sec. 3.2).
+ * max_restarts == 0: one m-step Arnoldi factorisation (Algorithm 1) with
+ * CGS2.  max_restarts > 0: Krylov-Schur (Sec. 3.2.2) of order m, restarted
+ * until the leading values have Ritz residual |b^T y| <= tol (Eq. 63) or
+ * max_restarts restarts were made.  Wanted set on restart: values with
+ * |mu| >= 1 - 0.05, clamped to [nev, m/2], never splitting a conjugate pair.
+ *   base_omega: device [ny][nx] or NULL (use the current base)
+ *   v0:         device [ny][nx] starting vector (need not be normalised)
+ *   m:          Krylov dimension, 2 <= m <= min(nx*ny - 1, 1024)
+ *   nev:        number of leading values wanted (rounded up by one when the
+ *               last one would split a complex-conjugate pair)
+ *   eig_re, eig_im, resid: host arrays of at least nev+1 entries: Ritz
+ *               values mu (eigenvalues of M, |mu| descending, then Im mu
+ *               descending) and their residuals
+ *   eigvecs:    device [nev+1][ny][nx] or NULL: Ritz vectors V y, unit
+ *               norm; a conjugate pair k, k+1 is stored as Re in slot k and
+ *               Im in slot k+1
+ *   n_eig:      host, number of values written (nev or nev+1)
+ *   n_conv:     host, how many of them have residual <= tol
+ *   n_matvec:   host, products with M made
+ * Allocates (n (m+1)) doubles of device memory for the basis for the
+ * duration of the call.  Returns NSSTAB_OK when all n_eig values converged,
+ * NSSTAB_NOT_CONVERGED otherwise.  Synchronous. */
+int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
+                 int m, int nev, double tol, int max_restarts, double T,
+                 double* eig_re, double* eig_im, double* resid, double* eigvecs,
+                 int* n_eig, int* n_conv, int* n_matvec);
+
+/* Measurement helper for the propagator of Eq. 42: run nsteps linearised
+ * steps from v (device [ny][nx]) about the current base flow, recording a
+ * CUDA event on the stepper's stream between consecutive kernels, and add
+ * the elapsed milliseconds of each of the six kernels of a step to
+ * kernel_ms[0..5] (host): column Poisson pass, row inverse of psi, row
+ * forward of the advection term, column AB2/CN update, row inverse of
+ * (omega*, psi*), row forward of the penalised vorticity.  The state the
+ * steps leave behind is discarded.  Synchronous. */
+int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, double* kernel_ms);
+
+/* One CGS2 orthogonalisation (Algorithm 1's Gram-Schmidt step applied
+ * twice): h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2;
+ * beta = ||w||.  V: device, j columns of length n with leading dimension
+ * ldv >= n (column k at V + k*ldv); w: device, n, in/out (NOT normalised);
+ * h: host, j entries; beta: host.  j may be 0 (only beta is computed).
+ * stream: cudaStream_t as void*.  The call keeps a small per-thread
+ * workspace (device partial sums, pinned host staging) that grows with j
+ * and lives until the process exits.  Synchronous. */
+int cgs2_orthogonalize(const double* V, long ldv, long n, int j, double* w,
+                       double* h, double* beta, void* stream);
+
+/* Host-only access to the dense FP64 eigen-solver that the Krylov layer
+ * applies to its projected matrix: eigenvalues and unit-norm eigenvectors
+ * (the Ritz pairs of H_m, Sec. 3.2.1) and the real Schur form reordered so
+ * that the eigenvalues with |lambda| >= thr come first (step 3 of the
+ * Krylov-Schur method, Sec. 3.2.2).  A, T, Z, vr, vi: HOST, column-major
+ * n x n; wr, wi: host, n.  Eigenvalues are in the diagonal order of the
+ * Schur form; column i of vr + i vi is the eigenvector of wr[i] + i wi[i]
+ * (vr, vi may be NULL).  is_hessenberg != 0 skips the Hessenberg reduction
+ * (A must then be upper Hessenberg).  *p receives the dimension of the
+ * leading block of wanted values.  No GPU is involved.  Errors:
+ * INVALID_ARG, NUMERICAL. */
+int nsstab_dense_eig(int n, const double* A, int is_hessenberg, double* wr, double* wi,
+                     double* vr, double* vi);
+int nsstab_dense_schur_ordered(int n, const double* A, double thr, double* T, double* Z, int* p);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* nsstab_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NSSTAB_H */

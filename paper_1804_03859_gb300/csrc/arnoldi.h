@@ -1,0 +1,23 @@
+// Internal interface of the Krylov eigen-driver (not part of the C ABI).
+#pragma once
+
+#include <complex>
+#include <vector>
+
+#include "stepper.cuh"
+
+namespace nsstab {
+
+struct ArnoldiOut {
+    std::vector<std::complex<double>> mu;   // leading Ritz values
+    std::vector<double> resid;              // |b^T y| of each
+    double* eigvecs = nullptr;              // device [k][n] or null
+    int n_eig = 0, n_conv = 0, n_matvec = 0, restarts = 0;
+    int status = NSSTAB_OK;
+};
+
+// v0: device n-vector; nsteps = T/dt linearised steps per product with M.
+int arnoldi_run(StepperBase* st, GsWork& gs, cudaStream_t stream, const nsstab_config& cfg, long n,
+                const double* v0, int m, int nev, double tol, int max_restarts, int nsteps, ArnoldiOut& out);
+
+}  // namespace nsstab

@@ -1,0 +1,180 @@
+// FP64 tall-skinny kernels of the Krylov layer: the classical Gram-Schmidt
+// products of Algorithm 1 (h = V^T w, w -= V h, applied twice = CGS2), norms
+// and the basis contraction V Q of the Krylov-Schur truncation / Ritz vector
+// assembly (Sec. 3.2.2).  The basis V is column-major: column k of length n
+// starts at V + k*ldv.  Reductions use a fixed grid and a fixed summation
+// order, so results are bit-reproducible run to run.
+#include <algorithm>
+#include <vector>
+
+#include "stepper.cuh"
+
+namespace nsstab {
+
+static const int kGsBlocks = 304;   // two blocks per SM on a 152-SM GB300
+static const int kGsThreads = 256;
+static const int kColGroup = 8;     // columns accumulated per pass over w
+
+// partial[b * ldp + c] = sum over block b's row range of V[c][i] * w[i], c < j
+__global__ void k_gs_dot(const double* __restrict__ V, long ldv, long n, int j,
+                         const double* __restrict__ w, double* __restrict__ partial, int ldp) {
+    const long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long r0 = (long)blockIdx.x * chunk;
+    const long r1 = min(n, r0 + chunk);
+    __shared__ double red[kColGroup][kGsThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < j; c0 += kColGroup) {
+        const int nc = min(kColGroup, j - c0);
+        double acc[kColGroup];
+#pragma unroll
+        for (int cc = 0; cc < kColGroup; ++cc) acc[cc] = 0.0;
+        for (long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const double wi = w[i];
+#pragma unroll
+            for (int cc = 0; cc < kColGroup; ++cc)
+                if (cc < nc) acc[cc] = fma(V[(long)(c0 + cc) * ldv + i], wi, acc[cc]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < kColGroup; ++cc) {
+            double a = acc[cc];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[cc][warp] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            double s = 0.0;
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += red[threadIdx.x][wv];
+            partial[(long)blockIdx.x * ldp + c0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// out[c] = sum_b partial[b * ldp + c]  (fixed order over b)
+__global__ void k_gs_reduce(const double* __restrict__ partial, int nb, int ldp, int j, double* __restrict__ out) {
+    for (int c = threadIdx.x; c < j; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += partial[(long)b * ldp + c];
+        out[c] = s;
+    }
+}
+
+// w[i] -= sum_c V[c][i] h[c]
+__global__ void k_gs_update(double* __restrict__ w, const double* __restrict__ V, long ldv, long n, int j,
+                            const double* __restrict__ h) {
+    extern __shared__ double hs[];
+    for (int c = threadIdx.x; c < j; c += blockDim.x) hs[c] = h[c];
+    __syncthreads();
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < j; ++c) acc = fma(V[(long)c * ldv + i], hs[c], acc);
+        w[i] -= acc;
+    }
+}
+
+__global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src, long n, double s) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = src[i] * s;
+}
+
+// out[c][i] = sum_k V[k][i] C[c*ldc + k], c < p  (out must not alias V)
+__global__ void k_combine(const double* __restrict__ V, long ldv, long n, int m, const double* __restrict__ C,
+                          int ldc, int p, double* __restrict__ out, long ldo) {
+    const int G = 8;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        for (int c0 = 0; c0 < p; c0 += G) {
+            double acc[G];
+#pragma unroll
+            for (int g = 0; g < G; ++g) acc[g] = 0.0;
+            for (int k = 0; k < m; ++k) {
+                const double v = V[(long)k * ldv + i];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    if (c0 + g < p) acc[g] = fma(v, __ldg(C + (long)(c0 + g) * ldc + k), acc[g]);
+            }
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+                if (c0 + g < p) out[(long)(c0 + g) * ldo + i] = acc[g];
+        }
+    }
+}
+
+int GsWork::alloc(int max_cols_) {
+    if (max_cols_ <= max_cols) return NSSTAB_OK;
+    release();
+    max_cols = max_cols_;
+    grid = kGsBlocks;
+    NS_CUDA(cudaMalloc(&partial, (size_t)grid * max_cols * sizeof(double)));
+    NS_CUDA(cudaMalloc(&hdev, (size_t)(2 * max_cols + 2) * sizeof(double)));
+    NS_CUDA(cudaMallocHost(&hhost, (size_t)(2 * max_cols + 2) * sizeof(double)));
+    return NSSTAB_OK;
+}
+
+void GsWork::release() {
+    if (partial) cudaFree(partial);
+    if (hdev) cudaFree(hdev);
+    if (hhost) cudaFreeHost(hhost);
+    partial = hdev = hhost = nullptr;
+    max_cols = 0;
+}
+
+static int dot_into(const double* V, long ldv, long n, int j, const double* w, double* out, GsWork& ws,
+                    cudaStream_t stream) {
+    k_gs_dot<<<ws.grid, kGsThreads, 0, stream>>>(V, ldv, n, j, w, ws.partial, ws.max_cols);
+    NS_LAUNCH_CHECK();
+    k_gs_reduce<<<1, 256, 0, stream>>>(ws.partial, ws.grid, ws.max_cols, j, out);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+static int update(double* w, const double* V, long ldv, long n, int j, const double* h, cudaStream_t stream) {
+    k_gs_update<<<kGsBlocks * 2, kGsThreads, j * sizeof(double), stream>>>(w, V, ldv, n, j, h);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+int cgs2(const double* V, long ldv, long n, int j, double* w, double* h, double* beta, GsWork& ws,
+         cudaStream_t stream) {
+    NS_TRY(ws.alloc(std::max(j, 1)));
+    double* h1 = ws.hdev;
+    double* h2 = ws.hdev + ws.max_cols;
+    double* b2 = ws.hdev + 2 * ws.max_cols;
+    if (j > 0) {
+        NS_TRY(dot_into(V, ldv, n, j, w, h1, ws, stream));
+        NS_TRY(update(w, V, ldv, n, j, h1, stream));
+        NS_TRY(dot_into(V, ldv, n, j, w, h2, ws, stream));
+        NS_TRY(update(w, V, ldv, n, j, h2, stream));
+    }
+    NS_TRY(dot_into(w, n, n, 1, w, b2, ws, stream));
+    NS_CUDA(cudaMemcpyAsync(ws.hhost, ws.hdev, (size_t)(2 * ws.max_cols + 1) * sizeof(double),
+                            cudaMemcpyDeviceToHost, stream));
+    NS_CUDA(cudaStreamSynchronize(stream));
+    for (int c = 0; c < j; ++c) h[c] = ws.hhost[c] + ws.hhost[ws.max_cols + c];
+    *beta = std::sqrt(ws.hhost[2 * ws.max_cols]);
+    return NSSTAB_OK;
+}
+
+int vec_norm(const double* x, long n, double* out, GsWork& ws, cudaStream_t stream) {
+    NS_TRY(ws.alloc(1));
+    double* b2 = ws.hdev + 2 * ws.max_cols;
+    NS_TRY(dot_into(x, n, n, 1, x, b2, ws, stream));
+    NS_CUDA(cudaMemcpyAsync(ws.hhost, b2, sizeof(double), cudaMemcpyDeviceToHost, stream));
+    NS_CUDA(cudaStreamSynchronize(stream));
+    *out = std::sqrt(ws.hhost[0]);
+    return NSSTAB_OK;
+}
+
+int vec_scale(double* dst, const double* src, long n, double s, cudaStream_t stream) {
+    k_scale<<<kGsBlocks, kGsThreads, 0, stream>>>(dst, src, n, s);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+int basis_combine(const double* V, long ldv, long n, int m, const double* C_dev, int p, double* out, long ldo,
+                  cudaStream_t stream) {
+    k_combine<<<kGsBlocks * 2, 128, 0, stream>>>(V, ldv, n, m, C_dev, m, p, out, ldo);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+}  // namespace nsstab

@@ -1,0 +1,865 @@
+// The vorticity-streamfunction time-stepper: kernels and host driver.
+//
+// One time step (nonlinear or linearised, Sec. 3, Eqs. 28-30) is six
+// kernels, alternating row passes (x-direction FFT of two real rows packed
+// into one complex transform, with the finite-difference stencil fused into
+// the forward pass) and column passes (y-direction FFT with the spectral
+// diagonal operators fused between the forward and inverse transforms):
+//
+//   col_poisson   X1 (x-spectrum of omega)  -> Wh = FFT2(omega), X2 = x-spectrum of psi
+//   row_inverse   X2                        -> P = psi
+//   row_forward   RHS: W, P (+ base)        -> X1 = x-spectrum of N
+//   col_update    X1, Wh, Nh                -> Nh = FFT2(N), X1/X2 = x-spectra of omega*, psi*
+//   row_inverse   X1, X2                    -> W = omega*, P = psi*
+//   row_forward   PEN: W, P (+ SFD state Y) -> W = omega^{n+1}, X1 = its x-spectrum
+//
+// Layouts: physical fields [ny][nx] (x fastest); every spectral array is
+// stored column-major [kx][ky] over the nx/2 packed x-wavenumbers, so the
+// column passes read and write contiguous columns.  The x-transform of a
+// real row is packed into nx/2 complex slots: slot 0 holds X[0] (real) in
+// .x and X[nx/2] (real) in .y.  In the column passes the packed kx = 0
+// column is the y-transform of (X0 + i XN); the spectral operators act on it
+// through its Hermitian halves (see apply_packed0).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fft.cuh"
+#include "stepper.cuh"
+
+namespace nsstab {
+
+enum RowMode { FWD_PLAIN = 0, FWD_RHS_NL = 1, FWD_RHS_LIN = 2, FWD_PEN_NL = 3, FWD_PEN_LIN = 4 };
+
+template <class T> struct Fields {
+    int nx, ny, nxh, logx, logy;
+    T idx2, idy2;          // 1/(2 dx), 1/(2 dy)
+    T Uinf;
+    T sfd_k1, sfd_k2;      // dt*chi_sfd, dt/Delta
+    T* W;                  // omega (physical)
+    T* P;                  // psi (physical)
+    T* Y;                  // SFD filtered state
+    const T* cS;           // s/(1+s), s = dt (chi/eta + sigma)
+    const T* cG;           // dt sigma Uinf / (1+s)
+    const T* Ub; const T* Vb; const T* DxOb; const T* DyOb;   // base-derived fields
+    Cx<T>* X1; Cx<T>* X2;  // x-spectral, y-physical [kx][y]
+    Cx<T>* Wh; Cx<T>* Nh;  // full spectra [kx][ky]
+    const T* tA; const T* tB; const T* tP;   // spectral operator tables [nxh+1][ny]
+    const Cx<T>* twx; const Cx<T>* twy;      // twiddles exp(-2 pi i e/N)
+};
+
+// ------------------------------------------------------------ point values
+
+template <class T, int MODE>
+__device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sfd) {
+    const int nx = f.nx, ny = f.ny;
+    const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
+    const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
+    const size_t c = (size_t)j * nx + i;
+    if (MODE == FWD_PLAIN) {
+        return f.W[c];
+    } else if (MODE == FWD_RHS_NL || MODE == FWD_RHS_LIN) {
+        const T* W = f.W;
+        const T* P = f.P;
+        const T dxw = (W[(size_t)j * nx + ip] - W[(size_t)j * nx + im]) * f.idx2;
+        const T dyw = (W[(size_t)jp * nx + i] - W[(size_t)jm * nx + i]) * f.idy2;
+        const T dyp = (P[(size_t)jp * nx + i] - P[(size_t)jm * nx + i]) * f.idy2;
+        const T dxp = (P[(size_t)j * nx + ip] - P[(size_t)j * nx + im]) * f.idx2;
+        if (MODE == FWD_RHS_NL) {
+            const T u = f.Uinf + dyp;
+            const T v = -dxp;
+            return -(u * dxw + v * dyw);
+        } else {
+            // N' = -(U_b D_x w + V_b D_y w + u' D_x Om_b + v' D_y Om_b)
+            return -(f.Ub[c] * dxw + f.Vb[c] * dyw + dyp * f.DxOb[c] - dxp * f.DyOb[c]);
+        }
+    } else {
+        // omega^{n+1} = omega* + D_x dv - D_y du with the implicit Brinkman +
+        // fringe velocity correction du = cG - cS u*, dv = -cS v*.
+        const T* P = f.P;
+        const T U = (MODE == FWD_PEN_NL) ? f.Uinf : T(0);
+        const int ipp = (i + 2) & (nx - 1), imm = (i - 2) & (nx - 1);
+        const int jpp = (j + 2) & (ny - 1), jmm = (j - 2) & (ny - 1);
+        const size_t rj = (size_t)j * nx;
+        // v* at (i+1, j) and (i-1, j)
+        const T vp = -((P[rj + ipp] - P[rj + i]) * f.idx2);
+        const T vm = -((P[rj + i] - P[rj + imm]) * f.idx2);
+        const T dvp = -f.cS[rj + ip] * vp;
+        const T dvm = -f.cS[rj + im] * vm;
+        // u* at (i, j+1) and (i, j-1)
+        const size_t cp = (size_t)jp * nx + i, cm = (size_t)jm * nx + i;
+        const T up = U + (P[(size_t)jpp * nx + i] - P[c]) * f.idy2;
+        const T um = U + (P[c] - P[(size_t)jmm * nx + i]) * f.idy2;
+        T dup = -f.cS[cp] * up;
+        T dum = -f.cS[cm] * um;
+        if (MODE == FWD_PEN_NL) {
+            dup += f.cG[cp];
+            dum += f.cG[cm];
+        }
+        T w = f.W[c] + (dvp - dvm) * f.idx2 - (dup - dum) * f.idy2;
+        if (sfd) {
+            const T y = f.Y[c];
+            const T d = w - y;
+            f.Y[c] = y + f.sfd_k2 * d;
+            w = w - f.sfd_k1 * d;
+        }
+        f.W[c] = w;
+        return w;
+    }
+}
+
+// -------------------------------------------------------------- row kernels
+
+// Forward x-transform of RP row pairs per block, with the row values made by
+// MODE.  Writes the packed half-spectra to X1 ([kx][y]) when do_fft.
+template <class T, int MODE>
+__global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
+    using C = Cx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int nx = f.nx, S = padded_len(nx);
+    const int pair0 = blockIdx.x * RP;
+    for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
+        const int p = e >> f.logx, i = e & (nx - 1);
+        const int j0 = 2 * (pair0 + p);
+        const T a = row_value<T, MODE>(f, i, j0, sfd);
+        const T b = row_value<T, MODE>(f, i, j0 + 1, sfd);
+        s[p * S + pad8(i)] = mk<T>(a, b);
+    }
+    if (!do_fft) return;
+    __syncthreads();
+    fft_smem<false, T>(s, f.logx, S, RP, f.twx, 0);
+    // split Z = FFT(a + i b) into the half-spectra of a and b
+    const int nh = nx >> 1;
+    for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
+        const int p = e & (RP - 1), k = e >> logRP;
+        const int j0 = 2 * (pair0 + p);
+        const C* z = s + p * S;
+        C A, B;
+        if (k == 0) {
+            const C z0 = z[0], zn = z[pad8(nh)];
+            A = mk<T>(z0.x, zn.x);
+            B = mk<T>(z0.y, zn.y);
+        } else {
+            const C zk = z[pad8(k)];
+            const C zm = cconj(z[pad8(nx - k)]);
+            A = cscale(cadd(zk, zm), T(0.5));
+            B = cscale(cmul_mi(csub(zk, zm)), T(0.5));
+        }
+        C* out = f.X1 + (size_t)k * f.ny + j0;
+        out[0] = A;
+        out[1] = B;
+    }
+}
+
+// Inverse x-transform of RP row pairs per block.  same: pair p = rows
+// (2p, 2p+1) of XA -> dA; otherwise pair p = row p of XA -> dA and row p of
+// XB -> dB.
+template <class T>
+__global__ void k_row_inverse(Fields<T> f, const Cx<T>* __restrict__ XA, const Cx<T>* __restrict__ XB,
+                              T* dA, T* dB, int RP, int logRP, bool same) {
+    using C = Cx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int nx = f.nx, ny = f.ny, nh = nx >> 1, S = padded_len(nx);
+    const int pair0 = blockIdx.x * RP;
+    for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
+        const int p = e & (RP - 1), k = e >> logRP;
+        const int pr = pair0 + p;
+        const int ra = same ? 2 * pr : pr;
+        const int rb = same ? 2 * pr + 1 : pr;
+        const C A = XA[(size_t)k * ny + ra];
+        const C B = (same ? XA : XB)[(size_t)k * ny + rb];
+        C* z = s + p * S;
+        if (k == 0) {
+            z[0] = mk<T>(A.x, B.x);
+            z[pad8(nh)] = mk<T>(A.y, B.y);
+        } else {
+            z[pad8(k)] = mk<T>(A.x - B.y, A.y + B.x);        // A + i B
+            z[pad8(nx - k)] = mk<T>(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
+        }
+    }
+    __syncthreads();
+    fft_smem<true, T>(s, f.logx, S, RP, f.twx, 0);
+    for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
+        const int p = e >> f.logx, i = e & (nx - 1);
+        const int pr = pair0 + p;
+        const int ra = same ? 2 * pr : pr;
+        const int rb = same ? 2 * pr + 1 : pr;
+        const C z = s[p * S + pad8(i)];
+        dA[(size_t)ra * nx + i] = z.x;
+        (same ? dA : dB)[(size_t)rb * nx + i] = z.y;
+    }
+}
+
+// ----------------------------------------------------------- column kernels
+
+// Packed kx = 0 column: Z = FFT_y(X0 + i XN).  Applying real operators f0 to
+// the kx = 0 part and fN to the kx = nx/2 part gives
+//   Z'(ky) = (f0 + fN)/2 Z(ky) + (f0 - fN)/2 conj(Z(-ky)).
+template <class C, class T>
+__device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
+    return cadd(cscale(z, T(0.5) * (f0 + fN)), cscale(zm_conj, T(0.5) * (f0 - fN)));
+}
+
+// Forward y-transform of CP columns of X1, store Wh, psi^ = scale * tP * omega^,
+// inverse y-transform into X2.
+template <class T>
+__global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
+    using C = Cx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s = reinterpret_cast<C*>(smem_raw);
+    const int ny = f.ny, S = padded_len(ny), logy = f.logy;
+    const int c0 = blockIdx.x * CP;
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, j = e & (ny - 1);
+        s[c * S + pad8(j)] = f.X1[(size_t)(c0 + c) * ny + j];
+    }
+    __syncthreads();
+    fft_smem<false, T>(s, logy, S, CP, f.twy, 0);
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, k = e & (ny - 1);
+        f.Wh[(size_t)(c0 + c) * ny + k] = s[c * S + pad8(k)];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, k = e & (ny - 1);
+        const int kx = c0 + c;
+        C* z = s + c * S;
+        if (kx != 0) {
+            z[pad8(k)] = cscale(z[pad8(k)], scale * f.tP[(size_t)kx * ny + k]);
+        } else if (k <= (ny >> 1)) {
+            const int km = (ny - k) & (ny - 1);
+            const T f0 = scale * f.tP[k], fN = scale * f.tP[(size_t)f.nxh * ny + k];
+            const C zk = z[pad8(k)], zm = z[pad8(km)];
+            z[pad8(k)] = apply_packed0(zk, cconj(zm), f0, fN);
+            if (km != k) z[pad8(km)] = apply_packed0(zm, cconj(zk), f0, fN);
+        }
+    }
+    __syncthreads();
+    fft_smem<true, T>(s, logy, S, CP, f.twy, 0);
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, j = e & (ny - 1);
+        f.X2[(size_t)(c0 + c) * ny + j] = s[c * S + pad8(j)];
+    }
+}
+
+// Forward y-transform of N (x-spectra in X1); AB2/AB1 + Crank-Nicolson update
+//   omega*^ = tA omega^ + tB (c1 N^n + c0 N^{n-1}),  psi*^ = tP omega*^
+// (tA, tB carry the 1/(nx ny) of the inverse transform); Nh <- N^n; inverse
+// y-transforms of omega*^ -> X1 and psi*^ -> X2.
+template <class T>
+__global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
+    using C = Cx<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* s1 = reinterpret_cast<C*>(smem_raw);
+    const int ny = f.ny, S = padded_len(ny), logy = f.logy;
+    C* s2 = s1 + (size_t)CP * S;
+    const int c0i = blockIdx.x * CP;
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, j = e & (ny - 1);
+        s1[c * S + pad8(j)] = f.X1[(size_t)(c0i + c) * ny + j];
+    }
+    __syncthreads();
+    fft_smem<false, T>(s1, logy, S, CP, f.twy, 0);
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, k = e & (ny - 1);
+        const int kx = c0i + c;
+        const size_t g = (size_t)kx * ny + k;
+        if (kx != 0) {
+            const C nn = s1[c * S + pad8(k)];
+            const C r = first ? cscale(nn, c1) : cadd(cscale(nn, c1), cscale(f.Nh[g], c0));
+            f.Nh[g] = nn;
+            const C ws = cadd(cscale(f.Wh[g], f.tA[g]), cscale(r, f.tB[g]));
+            s1[c * S + pad8(k)] = ws;
+            s2[c * S + pad8(k)] = cscale(ws, f.tP[g]);
+        } else if (k <= (ny >> 1)) {
+            const int km = (ny - k) & (ny - 1);
+            const size_t gN = (size_t)f.nxh * ny;
+            const C nk = s1[pad8(k)], nm = s1[pad8(km)];
+            C rk = cscale(nk, c1), rm = cscale(nm, c1);
+            if (!first) {
+                rk = cadd(rk, cscale(f.Nh[k], c0));
+                rm = cadd(rm, cscale(f.Nh[km], c0));
+            }
+            f.Nh[k] = nk;
+            f.Nh[km] = nm;
+            const C wk = f.Wh[k], wm = f.Wh[km];
+            const C wsk = cadd(apply_packed0(wk, cconj(wm), f.tA[k], f.tA[gN + k]),
+                               apply_packed0(rk, cconj(rm), f.tB[k], f.tB[gN + k]));
+            const C wsm = cadd(apply_packed0(wm, cconj(wk), f.tA[km], f.tA[gN + km]),
+                               apply_packed0(rm, cconj(rk), f.tB[km], f.tB[gN + km]));
+            s1[pad8(k)] = wsk;
+            s1[pad8(km)] = wsm;
+            s2[pad8(k)] = apply_packed0(wsk, cconj(wsm), f.tP[k], f.tP[gN + k]);
+            s2[pad8(km)] = apply_packed0(wsm, cconj(wsk), f.tP[km], f.tP[gN + km]);
+        }
+    }
+    __syncthreads();
+    fft_smem<true, T>(s1, logy, S, 2 * CP, f.twy, 0);
+    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
+        const int c = e >> logy, j = e & (ny - 1);
+        const size_t g = (size_t)(c0i + c) * ny + j;
+        f.X1[g] = s1[c * S + pad8(j)];
+        f.X2[g] = s2[c * S + pad8(j)];
+    }
+}
+
+// ------------------------------------------------------- pointwise kernels
+
+template <class T>
+__global__ void k_base_fields(Fields<T> f, T* Ub, T* Vb, T* DxOb, T* DyOb) {
+    const size_t n = (size_t)f.nx * f.ny;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(c & (f.nx - 1));
+        const int j = (int)(c >> f.logx);
+        const int ip = (i + 1) & (f.nx - 1), im = (i - 1) & (f.nx - 1);
+        const int jp = (j + 1) & (f.ny - 1), jm = (j - 1) & (f.ny - 1);
+        const T* P = f.P;   // Psi_b
+        const T* W = f.W;   // Omega_b
+        Ub[c] = f.Uinf + (P[(size_t)jp * f.nx + i] - P[(size_t)jm * f.nx + i]) * f.idy2;
+        Vb[c] = -((P[(size_t)j * f.nx + ip] - P[(size_t)j * f.nx + im]) * f.idx2);
+        DxOb[c] = (W[(size_t)j * f.nx + ip] - W[(size_t)j * f.nx + im]) * f.idx2;
+        DyOb[c] = (W[(size_t)jp * f.nx + i] - W[(size_t)jm * f.nx + i]) * f.idy2;
+    }
+}
+
+template <class A, class B>
+__global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, size_t n) {
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        dst[c] = (B)src[c];
+}
+
+// partial[b] = sum over this block's share of (a - b)^2, accumulated in FP64
+template <class T>
+__global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, size_t n, double* partial) {
+    double acc = 0.0;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
+        const double d = (double)a[c] - (double)b[c];
+        acc += d * d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    }
+}
+
+// ------------------------------------------------------------- host side
+
+struct Launch {
+    int blocks = 0, threads = 0, per = 0, logper = 0;
+    size_t smem = 0;
+};
+
+static const int kRedBlocks = 256;
+static const double kPi = 3.14159265358979323846;
+
+template <class T>
+class StepperImpl : public StepperBase {
+  public:
+    using C = Cx<T>;
+    StepperImpl(const nsstab_config& cfg, cudaStream_t s) : cfg_(cfg), stream_(s) {}
+    ~StepperImpl() override { release(); }
+
+    int init() override;
+    int poisson(const double* omega, double* psi) override;
+    int step_nonlinear(double* omega, int nsteps) override;
+    int set_base(const double* base_omega) override;
+    int step_linear(const double* v_in, double* v_out, int nsteps) override;
+    int residual(const double* q, double* r) override;
+    int sfd(double* omega, double chi, double Delta, double tol, long max_steps, int check_every,
+            double* r, long* steps) override;
+    int launches_per_step() const override { return kNumStepKernels; }
+    int profile_linear(const double* v, int nsteps, double* ms) override;
+
+  private:
+    nsstab_config cfg_;
+    cudaStream_t stream_;
+    Fields<T> f_{};
+    int nx_ = 0, ny_ = 0, nxh_ = 0;
+    size_t n_ = 0;
+    std::vector<void*> allocs_;
+    T* Wsave_ = nullptr;
+    C* Nhsave_ = nullptr;
+    double* red_ = nullptr;       // device partials
+    double* red_host_ = nullptr;  // pinned
+    bool have_base_ = false;
+    Launch lfwd_, linv_pairs_, linv_rows_, lcolp_, lcolu_;
+    T scale_ = T(1);
+
+    template <class P> int dalloc(P** p, size_t count) {
+        void* q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(P));
+        if (e != cudaSuccess) {
+            set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? NSSTAB_ERR_OUT_OF_MEMORY : NSSTAB_ERR_CUDA;
+        }
+        allocs_.push_back(q);
+        *p = static_cast<P*>(q);
+        return NSSTAB_OK;
+    }
+    void release() {
+        cudaStreamSynchronize(stream_);
+        for (void* p : allocs_) cudaFree(p);
+        allocs_.clear();
+        if (red_host_) cudaFreeHost(red_host_);
+        red_host_ = nullptr;
+    }
+    int build_tables();
+    Launch plan_rows(int npairs, size_t per_seq_bytes);
+    Launch plan_cols(int nseq_per_col, size_t per_seq_bytes);
+
+    int load(const double* src, T* dst);
+    int store(const T* src, double* dst);
+    int transform_W();                                   // X1 = x-spectrum of W
+    int stream_function();                               // Wh, X2, P from X1
+    int run_steps(int nsteps, bool linear, bool sfd, bool fft_last);
+    int sumsq_diff(const T* a, const T* b, double* out);
+};
+
+template <class T> Launch StepperImpl<T>::plan_rows(int npairs, size_t per_seq_bytes) {
+    // pairs per block: at least one warp of threads, then grow while enough
+    // blocks remain to fill the GPU twice over
+    const int per = nx_ / 8;
+    int rp = 1;
+    while (rp * per < 32 && 2 * rp <= npairs) rp *= 2;
+    while (2 * rp <= npairs && npairs / (2 * rp) >= 304 && 2 * rp * per <= 256 && 2 * rp * per_seq_bytes <= 96 * 1024)
+        rp *= 2;
+    Launch L;
+    L.per = rp;
+    L.logper = ilog2(rp);
+    L.blocks = npairs / rp;
+    L.threads = rp * per;
+    L.smem = rp * per_seq_bytes;
+    return L;
+}
+
+template <class T> Launch StepperImpl<T>::plan_cols(int nseq_per_col, size_t per_seq_bytes) {
+    const int per = ny_ / 8;
+    const int ncol = nxh_;
+    int cp = 1;
+    while (cp * per < 32 && 2 * cp <= ncol) cp *= 2;
+    while (2 * cp <= ncol && ncol / (2 * cp) >= 304 && 2 * cp * per <= 256 &&
+           2 * cp * nseq_per_col * per_seq_bytes <= 96 * 1024)
+        cp *= 2;
+    Launch L;
+    L.per = cp;
+    L.logper = ilog2(cp);
+    L.blocks = ncol / cp;
+    L.threads = cp * per;
+    L.smem = (size_t)cp * nseq_per_col * per_seq_bytes;
+    return L;
+}
+
+template <class T> int StepperImpl<T>::build_tables() {
+    const int nx = nx_, ny = ny_, nxh = nxh_;
+    const double dx = cfg_.Lx / nx, dy = cfg_.Ly / ny;
+    const double nu = 1.0 / cfg_.Re, dt = cfg_.dt;
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    // twiddles exp(-2 pi i e / N) in extended precision, rounded once
+    std::vector<C> twx(nx), twy(ny);
+    for (int e = 0; e < nx; ++e) {
+        long double a = two_pi * (long double)e / (long double)nx;
+        twx[e] = mk<T>((T)cosl(a), (T)(-sinl(a)));
+    }
+    for (int e = 0; e < ny; ++e) {
+        long double a = two_pi * (long double)e / (long double)ny;
+        twy[e] = mk<T>((T)cosl(a), (T)(-sinl(a)));
+    }
+    // spectral operators over kx in [0, nx/2], ky in [0, ny): eigenvalue of
+    // the periodic 5-point Laplacian lam = lx(kx) + ly(ky)
+    const size_t nt = (size_t)(nxh + 1) * ny;
+    std::vector<T> tA(nt), tB(nt), tP(nt);
+    const double scale = 1.0 / ((double)nx * (double)ny);
+    for (int kx = 0; kx <= nxh; ++kx) {
+        const double sx = std::sin(kPi * kx / nx);
+        const double lx = -(4.0 / (dx * dx)) * sx * sx;
+        for (int ky = 0; ky < ny; ++ky) {
+            const double sy = std::sin(kPi * ky / ny);
+            const double lam = lx - (4.0 / (dy * dy)) * sy * sy;
+            const size_t g = (size_t)kx * ny + ky;
+            if (kx == 0 && ky == 0) {
+                tA[g] = tB[g] = tP[g] = T(0);
+                continue;
+            }
+            const double a = 1.0 + 0.5 * nu * dt * lam;
+            const double b = 1.0 - 0.5 * nu * dt * lam;
+            tA[g] = (T)(scale * a / b);
+            tB[g] = (T)(scale * dt / b);
+            tP[g] = (T)(-1.0 / lam);
+        }
+    }
+    // penalisation coefficients from the cylinder mask and the fringe
+    std::vector<T> cS(n_), cG(n_);
+    const double R = 0.5 * cfg_.cyl_D, w = 0.5 * cfg_.mask_cells * dx;
+    const double xs = (1.0 - cfg_.sponge_frac) * cfg_.Lx;
+    for (int j = 0; j < ny; ++j) {
+        const double y = j * dy;
+        for (int i = 0; i < nx; ++i) {
+            const double x = i * dx;
+            double chi = 0.0;
+            if (cfg_.cyl_D > 0.0) {
+                double ddx = std::fmod(x - cfg_.cyl_x + 0.5 * cfg_.Lx, cfg_.Lx);
+                if (ddx < 0) ddx += cfg_.Lx;
+                ddx -= 0.5 * cfg_.Lx;
+                double ddy = std::fmod(y - cfg_.cyl_y + 0.5 * cfg_.Ly, cfg_.Ly);
+                if (ddy < 0) ddy += cfg_.Ly;
+                ddy -= 0.5 * cfg_.Ly;
+                const double r = std::sqrt(ddx * ddx + ddy * ddy);
+                if (r <= R - w) chi = 1.0;
+                else if (r >= R + w) chi = 0.0;
+                else chi = 0.5 * (1.0 - std::sin(kPi * (r - R) / (2.0 * w)));
+            }
+            double sig = 0.0;
+            if (cfg_.sponge_sigma > 0.0 && cfg_.sponge_frac > 0.0 && x >= xs) {
+                const double sn = std::sin(kPi * (x - xs) / (cfg_.sponge_frac * cfg_.Lx));
+                sig = cfg_.sponge_sigma * sn * sn;
+            }
+            const double s = dt * (chi / cfg_.eta + sig);
+            cS[(size_t)j * nx + i] = (T)(s / (1.0 + s));
+            cG[(size_t)j * nx + i] = (T)(dt * sig * cfg_.Uinf / (1.0 + s));
+        }
+    }
+    NS_CUDA(cudaMemcpyAsync((void*)f_.twx, twx.data(), nx * sizeof(C), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.twy, twy.data(), ny * sizeof(C), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.tA, tA.data(), nt * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.tB, tB.data(), nt * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.tP, tP.data(), nt * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.cS, cS.data(), n_ * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.cG, cG.data(), n_ * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaStreamSynchronize(stream_));   // host vectors go out of scope
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::init() {
+    nx_ = cfg_.nx;
+    ny_ = cfg_.ny;
+    nxh_ = nx_ / 2;
+    n_ = (size_t)nx_ * ny_;
+    const size_t nc = (size_t)nxh_ * ny_;
+    f_.nx = nx_;
+    f_.ny = ny_;
+    f_.nxh = nxh_;
+    f_.logx = ilog2(nx_);
+    f_.logy = ilog2(ny_);
+    f_.idx2 = (T)(1.0 / (2.0 * cfg_.Lx / nx_));
+    f_.idy2 = (T)(1.0 / (2.0 * cfg_.Ly / ny_));
+    f_.Uinf = (T)cfg_.Uinf;
+    scale_ = (T)(1.0 / ((double)nx_ * (double)ny_));
+    T *W, *P, *cS, *cG, *tA, *tB, *tP;
+    C *X1, *X2, *Wh, *Nh, *twx, *twy;
+    const size_t nt = (size_t)(nxh_ + 1) * ny_;
+    NS_TRY(dalloc(&W, n_));
+    NS_TRY(dalloc(&P, n_));
+    NS_TRY(dalloc(&cS, n_));
+    NS_TRY(dalloc(&cG, n_));
+    NS_TRY(dalloc(&X1, nc));
+    NS_TRY(dalloc(&X2, nc));
+    NS_TRY(dalloc(&Wh, nc));
+    NS_TRY(dalloc(&Nh, nc));
+    NS_TRY(dalloc(&tA, nt));
+    NS_TRY(dalloc(&tB, nt));
+    NS_TRY(dalloc(&tP, nt));
+    NS_TRY(dalloc(&twx, (size_t)nx_));
+    NS_TRY(dalloc(&twy, (size_t)ny_));
+    NS_TRY(dalloc(&red_, (size_t)kRedBlocks));
+    NS_CUDA(cudaMallocHost((void**)&red_host_, kRedBlocks * sizeof(double)));
+    f_.W = W; f_.P = P; f_.cS = cS; f_.cG = cG;
+    f_.X1 = X1; f_.X2 = X2; f_.Wh = Wh; f_.Nh = Nh;
+    f_.tA = tA; f_.tB = tB; f_.tP = tP;
+    f_.twx = twx; f_.twy = twy;
+    f_.Y = nullptr;
+    f_.Ub = f_.Vb = f_.DxOb = f_.DyOb = nullptr;
+    NS_TRY(build_tables());
+
+    const size_t sx = padded_len(nx_) * sizeof(C), sy = padded_len(ny_) * sizeof(C);
+    lfwd_ = plan_rows(ny_ / 2, sx);
+    linv_pairs_ = plan_rows(ny_ / 2, sx);
+    linv_rows_ = plan_rows(ny_, sx);
+    lcolp_ = plan_cols(1, sy);
+    lcolu_ = plan_cols(2, sy);
+    const size_t big = 200 * 1024;
+    if (lfwd_.smem > big || linv_rows_.smem > big || lcolu_.smem > big) {
+        set_error("grid too large for the shared-memory FFT");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
+    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_RHS_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
+    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_RHS_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
+    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_PEN_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
+    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_PEN_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
+    const size_t inv_smem = linv_rows_.smem > linv_pairs_.smem ? linv_rows_.smem : linv_pairs_.smem;
+    NS_CUDA(cudaFuncSetAttribute(k_row_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
+    NS_CUDA(cudaFuncSetAttribute(k_col_poisson<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lcolp_.smem));
+    NS_CUDA(cudaFuncSetAttribute(k_col_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lcolu_.smem));
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::load(const double* src, T* dst) {
+    if (sizeof(T) == sizeof(double)) {
+        NS_CUDA(cudaMemcpyAsync(dst, src, n_ * sizeof(double), cudaMemcpyDeviceToDevice, stream_));
+    } else {
+        k_convert<double, T><<<304, 256, 0, stream_>>>(src, dst, n_);
+        NS_LAUNCH_CHECK();
+    }
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::store(const T* src, double* dst) {
+    if (sizeof(T) == sizeof(double)) {
+        NS_CUDA(cudaMemcpyAsync(dst, src, n_ * sizeof(double), cudaMemcpyDeviceToDevice, stream_));
+    } else {
+        k_convert<T, double><<<304, 256, 0, stream_>>>(src, dst, n_);
+        NS_LAUNCH_CHECK();
+    }
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::transform_W() {
+    k_row_forward<T, FWD_PLAIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::stream_function() {
+    k_col_poisson<T><<<lcolp_.blocks, lcolp_.threads, lcolp_.smem, stream_>>>(f_, lcolp_.per, scale_);
+    NS_LAUNCH_CHECK();
+    k_row_inverse<T><<<linv_pairs_.blocks, linv_pairs_.threads, linv_pairs_.smem, stream_>>>(
+        f_, f_.X2, f_.X2, f_.P, f_.P, linv_pairs_.per, linv_pairs_.logper, true);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::run_steps(int nsteps, bool linear, bool sfd, bool fft_last) {
+    if (linear && !have_base_) {
+        set_error("linearised step requested before a base flow was set");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    for (int s = 0; s < nsteps; ++s) {
+        const bool first = (s == 0);
+        NS_TRY(stream_function());
+        if (linear)
+            k_row_forward<T, FWD_RHS_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
+        else
+            k_row_forward<T, FWD_RHS_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
+        NS_LAUNCH_CHECK();
+        const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
+        k_col_update<T><<<lcolu_.blocks, lcolu_.threads, lcolu_.smem, stream_>>>(f_, lcolu_.per, c1, c0, first);
+        NS_LAUNCH_CHECK();
+        k_row_inverse<T><<<linv_rows_.blocks, linv_rows_.threads, linv_rows_.smem, stream_>>>(
+            f_, f_.X1, f_.X2, f_.W, f_.P, linv_rows_.per, linv_rows_.logper, false);
+        NS_LAUNCH_CHECK();
+        const bool do_fft = fft_last || (s + 1 < nsteps);
+        if (linear)
+            k_row_forward<T, FWD_PEN_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, sfd, do_fft);
+        else
+            k_row_forward<T, FWD_PEN_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, sfd, do_fft);
+        NS_LAUNCH_CHECK();
+    }
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::profile_linear(const double* v, int nsteps, double* ms) {
+    if (!have_base_) {
+        set_error("profile: no base flow set");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    cudaEvent_t ev[kNumStepKernels + 1];
+    for (int k = 0; k <= kNumStepKernels; ++k) NS_CUDA(cudaEventCreate(&ev[k]));
+    for (int k = 0; k < kNumStepKernels; ++k) ms[k] = 0.0;
+    int rc = load(v, f_.W);
+    if (rc == NSSTAB_OK) rc = transform_W();
+    for (int s = 0; s < nsteps && rc == NSSTAB_OK; ++s) {
+        const bool first = (s == 0);
+        const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
+        cudaEventRecord(ev[0], stream_);
+        k_col_poisson<T><<<lcolp_.blocks, lcolp_.threads, lcolp_.smem, stream_>>>(f_, lcolp_.per, scale_);
+        cudaEventRecord(ev[1], stream_);
+        k_row_inverse<T><<<linv_pairs_.blocks, linv_pairs_.threads, linv_pairs_.smem, stream_>>>(
+            f_, f_.X2, f_.X2, f_.P, f_.P, linv_pairs_.per, linv_pairs_.logper, true);
+        cudaEventRecord(ev[2], stream_);
+        k_row_forward<T, FWD_RHS_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
+        cudaEventRecord(ev[3], stream_);
+        k_col_update<T><<<lcolu_.blocks, lcolu_.threads, lcolu_.smem, stream_>>>(f_, lcolu_.per, c1, c0, first);
+        cudaEventRecord(ev[4], stream_);
+        k_row_inverse<T><<<linv_rows_.blocks, linv_rows_.threads, linv_rows_.smem, stream_>>>(
+            f_, f_.X1, f_.X2, f_.W, f_.P, linv_rows_.per, linv_rows_.logper, false);
+        cudaEventRecord(ev[5], stream_);
+        k_row_forward<T, FWD_PEN_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
+        cudaEventRecord(ev[6], stream_);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+        if (e != cudaSuccess) {
+            set_error(std::string("profile: ") + cudaGetErrorString(e));
+            rc = NSSTAB_ERR_CUDA;
+            break;
+        }
+        for (int k = 0; k < kNumStepKernels; ++k) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            ms[k] += t;
+        }
+    }
+    for (int k = 0; k <= kNumStepKernels; ++k) cudaEventDestroy(ev[k]);
+    return rc;
+}
+
+template <class T> int StepperImpl<T>::poisson(const double* omega, double* psi) {
+    NS_TRY(load(omega, f_.W));
+    NS_TRY(transform_W());
+    NS_TRY(stream_function());
+    return store(f_.P, psi);
+}
+
+template <class T> int StepperImpl<T>::step_nonlinear(double* omega, int nsteps) {
+    NS_TRY(load(omega, f_.W));
+    if (nsteps > 0) {
+        NS_TRY(transform_W());
+        NS_TRY(run_steps(nsteps, false, false, false));
+    }
+    return store(f_.W, omega);
+}
+
+template <class T> int StepperImpl<T>::set_base(const double* base_omega) {
+    if (!f_.Ub) {
+        T *Ub, *Vb, *DxOb, *DyOb;
+        NS_TRY(dalloc(&Ub, n_));
+        NS_TRY(dalloc(&Vb, n_));
+        NS_TRY(dalloc(&DxOb, n_));
+        NS_TRY(dalloc(&DyOb, n_));
+        f_.Ub = Ub; f_.Vb = Vb; f_.DxOb = DxOb; f_.DyOb = DyOb;
+    }
+    NS_TRY(load(base_omega, f_.W));
+    NS_TRY(transform_W());
+    NS_TRY(stream_function());   // P = Psi_b
+    k_base_fields<T><<<304, 256, 0, stream_>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb, (T*)f_.DyOb);
+    NS_LAUNCH_CHECK();
+    have_base_ = true;
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::step_linear(const double* v_in, double* v_out, int nsteps) {
+    NS_TRY(load(v_in, f_.W));
+    if (nsteps > 0) {
+        NS_TRY(transform_W());
+        NS_TRY(run_steps(nsteps, true, false, false));
+    }
+    return store(f_.W, v_out);
+}
+
+template <class T> int StepperImpl<T>::sumsq_diff(const T* a, const T* b, double* out) {
+    k_diff_sumsq<T><<<kRedBlocks, 256, 0, stream_>>>(a, b, n_, red_);
+    NS_LAUNCH_CHECK();
+    NS_CUDA(cudaMemcpyAsync(red_host_, red_, kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    NS_CUDA(cudaStreamSynchronize(stream_));
+    double s = 0.0;
+    for (int b2 = 0; b2 < kRedBlocks; ++b2) s += red_host_[b2];
+    *out = s;
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::residual(const double* q, double* r) {
+    if (!Wsave_) NS_TRY(dalloc(&Wsave_, n_));
+    NS_TRY(load(q, f_.W));
+    NS_CUDA(cudaMemcpyAsync(Wsave_, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+    NS_TRY(transform_W());
+    NS_TRY(run_steps(1, false, false, false));
+    double ss = 0.0;
+    NS_TRY(sumsq_diff(f_.W, Wsave_, &ss));
+    const double dx = cfg_.Lx / nx_, dy = cfg_.Ly / ny_;
+    *r = std::sqrt(ss * dx * dy) / cfg_.dt;
+    return NSSTAB_OK;
+}
+
+template <class T>
+int StepperImpl<T>::sfd(double* omega, double chi, double Delta, double tol, long max_steps, int check_every,
+                        double* r_out, long* steps_out) {
+    if (!f_.Y) {
+        T* Y;
+        NS_TRY(dalloc(&Y, n_));
+        f_.Y = Y;
+    }
+    if (!Wsave_) NS_TRY(dalloc(&Wsave_, n_));
+    if (!Nhsave_) NS_TRY(dalloc(&Nhsave_, (size_t)nxh_ * ny_));
+    f_.sfd_k1 = (T)(cfg_.dt * chi);
+    f_.sfd_k2 = (T)(cfg_.dt / Delta);
+    NS_TRY(load(omega, f_.W));
+    NS_CUDA(cudaMemcpyAsync(f_.Y, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+    NS_TRY(transform_W());
+    const double dx = cfg_.Lx / nx_, dy = cfg_.Ly / ny_;
+    long k = 0;
+    double r = INFINITY;
+    int status = NSSTAB_NOT_CONVERGED;
+    bool first_chunk = true;
+    const size_t nc = (size_t)nxh_ * ny_;
+    while (k < max_steps) {
+        const long chunk = std::min<long>(check_every, max_steps - k);
+        // the AB2 history continues across chunks: only the very first step is AB1
+        for (long s = 0; s < chunk; ++s) {
+            const bool first = first_chunk && s == 0;
+            NS_TRY(stream_function());
+            k_row_forward<T, FWD_RHS_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
+            NS_LAUNCH_CHECK();
+            const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
+            k_col_update<T><<<lcolu_.blocks, lcolu_.threads, lcolu_.smem, stream_>>>(f_, lcolu_.per, c1, c0, first);
+            NS_LAUNCH_CHECK();
+            k_row_inverse<T><<<linv_rows_.blocks, linv_rows_.threads, linv_rows_.smem, stream_>>>(
+                f_, f_.X1, f_.X2, f_.W, f_.P, linv_rows_.per, linv_rows_.logper, false);
+            NS_LAUNCH_CHECK();
+            k_row_forward<T, FWD_PEN_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, true, true);
+            NS_LAUNCH_CHECK();
+        }
+        first_chunk = false;
+        k += chunk;
+        // residual of the current X with one plain AB1 step, then restore the state
+        NS_CUDA(cudaMemcpyAsync(Wsave_, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+        NS_CUDA(cudaMemcpyAsync(Nhsave_, f_.Nh, nc * sizeof(C), cudaMemcpyDeviceToDevice, stream_));
+        NS_TRY(run_steps(1, false, false, false));
+        double ss = 0.0;
+        NS_TRY(sumsq_diff(f_.W, Wsave_, &ss));
+        r = std::sqrt(ss * dx * dy) / cfg_.dt;
+        NS_CUDA(cudaMemcpyAsync(f_.W, Wsave_, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+        NS_CUDA(cudaMemcpyAsync(f_.Nh, Nhsave_, nc * sizeof(C), cudaMemcpyDeviceToDevice, stream_));
+        NS_TRY(transform_W());
+        if (!std::isfinite(r)) {
+            status = NSSTAB_DIVERGED;
+            break;
+        }
+        if (r <= tol) {
+            status = NSSTAB_OK;
+            break;
+        }
+    }
+    NS_TRY(store(f_.W, omega));
+    NS_CUDA(cudaStreamSynchronize(stream_));
+    *r_out = r;
+    *steps_out = k;
+    return status;
+}
+
+int validate_config(const nsstab_config& c) {
+    auto bad = [](const char* m) {
+        set_error(m);
+        return NSSTAB_ERR_INVALID_ARG;
+    };
+    if (!is_pow2(c.nx) || !is_pow2(c.ny) || c.nx < 8 || c.ny < 8 || c.nx > 4096 || c.ny > 4096)
+        return bad("nx and ny must be powers of two in [8, 4096]");
+    if (!(c.Lx > 0) || !(c.Ly > 0) || !(c.dt > 0) || !(c.Re > 0)) return bad("Lx, Ly, dt and Re must be positive");
+    if (c.cyl_D > 0 && !(c.eta > 0)) return bad("eta must be positive when the cylinder is enabled");
+    if (c.cyl_D > 0 && !(c.mask_cells > 0)) return bad("mask_cells must be positive");
+    if (c.sponge_sigma > 0 && !(c.sponge_frac > 0 && c.sponge_frac <= 1)) return bad("sponge_frac must be in (0, 1]");
+    if (c.precision != 64 && c.precision != 32) return bad("precision must be 64 or 32");
+    return NSSTAB_OK;
+}
+
+StepperBase* make_stepper(const nsstab_config& cfg, cudaStream_t stream) {
+    if (cfg.precision == 32) return new StepperImpl<float>(cfg, stream);
+    return new StepperImpl<double>(cfg, stream);
+}
+
+}  // namespace nsstab

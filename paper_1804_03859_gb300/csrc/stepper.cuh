@@ -1,0 +1,50 @@
+// Internal interface of the time-stepper (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace nsstab {
+
+// Precision-independent face of a stepper; StepperImpl<T> implements it for
+// T = double (FP64 stepper) and T = float (FP32 stepper with FP64 I/O).
+struct StepperBase {
+    virtual ~StepperBase() {}
+    virtual int init() = 0;
+    virtual int poisson(const double* omega, double* psi) = 0;
+    virtual int step_nonlinear(double* omega, int nsteps) = 0;
+    virtual int set_base(const double* base_omega) = 0;
+    virtual int step_linear(const double* v_in, double* v_out, int nsteps) = 0;
+    virtual int residual(const double* q, double* r) = 0;
+    virtual int sfd(double* omega, double chi, double Delta, double tol, long max_steps,
+                    int check_every, double* r, long* steps) = 0;
+    virtual int launches_per_step() const = 0;
+    // time each kernel of `nsteps` linearised steps from v with CUDA events
+    // on the stepper's stream; ms[k] accumulates kernel k (kNumStepKernels)
+    virtual int profile_linear(const double* v, int nsteps, double* ms) = 0;
+};
+
+constexpr int kNumStepKernels = 6;   // col_poisson, row_inverse(psi), row_forward(rhs),
+                                     // col_update, row_inverse(omega*, psi*), row_forward(pen)
+StepperBase* make_stepper(const nsstab_config& cfg, cudaStream_t stream);
+int validate_config(const nsstab_config& cfg);
+
+// Krylov helpers (krylov_kernels.cu), all FP64 on `stream`.
+struct GsWork {
+    double* partial = nullptr;   // [grid][max_cols]
+    double* hdev = nullptr;      // [2][max_cols]
+    double* hhost = nullptr;     // pinned [2*max_cols + 2]
+    int grid = 0;
+    int max_cols = 0;
+    int alloc(int max_cols_);
+    void release();
+};
+int cgs2(const double* V, long ldv, long n, int j, double* w, double* h, double* beta,
+         GsWork& ws, cudaStream_t stream);
+int vec_norm(const double* x, long n, double* out, GsWork& ws, cudaStream_t stream);
+int vec_scale(double* dst, const double* src, long n, double s, cudaStream_t stream);
+// out[:, c] = sum_k V[:, k] C[k, c] for c < p (C: device, column-major
+// m x p); out must not alias V.
+int basis_combine(const double* V, long ldv, long n, int m, const double* C_dev, int p,
+                  double* out, long ldo, cudaStream_t stream);
+
+}  // namespace nsstab

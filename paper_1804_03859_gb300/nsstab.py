@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libnsstab.so (C ABI in include/nsstab.h).
+
+Argument marshalling only: every step of the method runs in the library.
+Device fields are ``torch.Tensor`` objects (CUDA, float64, contiguous,
+shape ``[ny, nx]``); PyTorch supplies the device memory and the stream.  The
+functions carry the C names; ``Stepper`` is a convenience owner of a
+``nsstab_stepper*``.  There is no CPU fallback: if the library is missing
+or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libnsstab.so")
+
+OK = 0
+NOT_CONVERGED = 1
+DIVERGED = 2
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+_lp = ctypes.POINTER(ctypes.c_long)
+
+
+class Config(ctypes.Structure):
+    """Mirror of ``nsstab_config``."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("Lx", ctypes.c_double), ("Ly", ctypes.c_double),
+        ("dt", ctypes.c_double), ("Re", ctypes.c_double), ("Uinf", ctypes.c_double),
+        ("cyl_x", ctypes.c_double), ("cyl_y", ctypes.c_double), ("cyl_D", ctypes.c_double),
+        ("eta", ctypes.c_double), ("mask_cells", ctypes.c_double),
+        ("sponge_frac", ctypes.c_double), ("sponge_sigma", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+# (name, restype, argtypes) of every exported symbol declared in nsstab.h
+SIGNATURES = [
+    ("nsstab_config_default", None, [ctypes.POINTER(Config)]),
+    ("stepper_create", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("stepper_destroy", None, [ctypes.c_void_p]),
+    ("stepper_poisson", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("step_nonlinear", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    ("stepper_set_base", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("apply_expTL", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    ("stepper_residual", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _dp]),
+    ("sfd_baseflow", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_long, ctypes.c_int, _dp, _lp]),
+    ("arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                    ctypes.c_void_p, _ip, _ip, _ip]),
+    ("stepper_profile_linear", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _dp]),
+    ("cgs2_orthogonalize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
+                                          ctypes.c_void_p, _dp, _dp, ctypes.c_void_p]),
+    ("nsstab_dense_eig", ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]),
+    ("nsstab_dense_schur_ordered", ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_double, _dp, _dp, _ip]),
+    ("nsstab_last_error", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libnsstab.so (build it with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} not found: build the CUDA library first (__graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class NsstabError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str, allow_soft: bool = False) -> int:
+    if rc < 0 or (rc > 0 and not allow_soft):
+        msg = load_library().nsstab_last_error().decode(errors="replace")
+        raise NsstabError(f"{what} failed with status {rc}: {msg}")
+    return rc
+
+
+def _field_ptr(t, shape, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.device.type != "cuda" or t.dtype != torch.float64 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor")
+    if tuple(t.shape[-2:]) != tuple(shape) or t.numel() % (shape[0] * shape[1]) != 0:
+        raise ValueError(f"{name} must have shape {shape}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _cfg_from(**kw) -> Config:
+    cfg = Config()
+    load_library().nsstab_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        if not hasattr(cfg, k):
+            raise KeyError(k)
+        setattr(cfg, k, v)
+    return cfg
+
+
+def config_default() -> Config:
+    return _cfg_from()
+
+
+def current_stream_handle():
+    import torch
+
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+# ------------------------------------------------ C-named thin wrappers
+
+def stepper_create(cfg: Config, stream=None) -> ctypes.c_void_p:
+    lib = load_library()
+    h = ctypes.c_void_p()
+    s = current_stream_handle() if stream is None else ctypes.c_void_p(stream)
+    _check(lib.stepper_create(ctypes.byref(cfg), s, ctypes.byref(h)), "stepper_create")
+    return h
+
+
+def stepper_destroy(h) -> None:
+    load_library().stepper_destroy(h)
+
+
+def cgs2_orthogonalize(V, n: int, j: int, w, ldv: int | None = None, stream=None):
+    """One CGS2 step on device tensors: returns (h as numpy array, beta)."""
+    import torch
+
+    lib = load_library()
+    if w.dtype != torch.float64 or w.device.type != "cuda" or not w.is_contiguous():
+        raise ValueError("w must be a contiguous float64 CUDA tensor")
+    if j > 0 and (V.dtype != torch.float64 or V.device.type != "cuda" or not V.is_contiguous()):
+        raise ValueError("V must be a contiguous float64 CUDA tensor")
+    h = np.zeros(max(j, 1))
+    beta = ctypes.c_double()
+    s = current_stream_handle() if stream is None else ctypes.c_void_p(stream)
+    vp = ctypes.c_void_p(V.data_ptr()) if j > 0 else ctypes.c_void_p(0)
+    _check(lib.cgs2_orthogonalize(vp, ldv if ldv is not None else n, n, j, ctypes.c_void_p(w.data_ptr()),
+                                  h.ctypes.data_as(_dp), ctypes.byref(beta), s), "cgs2_orthogonalize")
+    return h[:j], beta.value
+
+
+def dense_eig(A: np.ndarray, is_hessenberg: bool = False, vectors: bool = True):
+    """Host eigen-solver of the library on a small dense matrix (no GPU)."""
+    lib = load_library()
+    A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    wr, wi = np.zeros(n), np.zeros(n)
+    vr = np.zeros((n, n), order="F") if vectors else None
+    vi = np.zeros((n, n), order="F") if vectors else None
+    _check(lib.nsstab_dense_eig(n, A.ctypes.data_as(_dp), int(is_hessenberg), wr.ctypes.data_as(_dp),
+                                wi.ctypes.data_as(_dp), vr.ctypes.data_as(_dp) if vectors else None,
+                                vi.ctypes.data_as(_dp) if vectors else None), "nsstab_dense_eig")
+    w = wr + 1j * wi
+    return (w, vr + 1j * vi) if vectors else w
+
+
+def dense_schur_ordered(A: np.ndarray, thr: float):
+    """Real Schur form with the eigenvalues |lambda| >= thr first: (T, Z, p)."""
+    lib = load_library()
+    A = np.asfortranarray(np.asarray(A, dtype=np.float64))
+    n = A.shape[0]
+    T = np.zeros((n, n), order="F")
+    Z = np.zeros((n, n), order="F")
+    p = ctypes.c_int()
+    _check(lib.nsstab_dense_schur_ordered(n, A.ctypes.data_as(_dp), float(thr), T.ctypes.data_as(_dp),
+                                          Z.ctypes.data_as(_dp), ctypes.byref(p)), "nsstab_dense_schur_ordered")
+    return T, Z, p.value
+
+
+@dataclass
+class EigResult:
+    mu: np.ndarray          # Ritz values (eigenvalues of M)
+    residual: np.ndarray    # |b^T y|
+    n_conv: int
+    n_matvec: int
+    status: int
+
+    def growth(self, T: float) -> np.ndarray:
+        """lambda = log(mu)/T (eigenvalues of the linearised operator)."""
+        return np.log(self.mu.astype(complex)) / T
+
+
+class Stepper:
+    """Owner of one ``nsstab_stepper`` bound to the current torch stream."""
+
+    def __init__(self, **cfg):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("nsstab needs a CUDA GPU")
+        self.cfg = _cfg_from(**cfg)
+        self.shape = (self.cfg.ny, self.cfg.nx)
+        self._stream = torch.cuda.current_stream()
+        self._h = stepper_create(self.cfg, self._stream.cuda_stream)
+        self._lib = load_library()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.stepper_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _p(self, t, name):
+        return _field_ptr(t, self.shape, name)
+
+    def stepper_poisson(self, omega, psi):
+        _check(self._lib.stepper_poisson(self._h, self._p(omega, "omega"), self._p(psi, "psi")), "stepper_poisson")
+
+    def step_nonlinear(self, omega, nsteps: int):
+        _check(self._lib.step_nonlinear(self._h, self._p(omega, "omega"), int(nsteps)), "step_nonlinear")
+
+    def stepper_set_base(self, base):
+        _check(self._lib.stepper_set_base(self._h, self._p(base, "base")), "stepper_set_base")
+
+    def apply_expTL(self, base, v_in, v_out, T: float):
+        bp = self._p(base, "base") if base is not None else None
+        _check(self._lib.apply_expTL(self._h, bp, self._p(v_in, "v_in"), self._p(v_out, "v_out"), float(T)),
+               "apply_expTL")
+
+    def stepper_residual(self, q) -> float:
+        r = ctypes.c_double()
+        _check(self._lib.stepper_residual(self._h, self._p(q, "q"), ctypes.byref(r)), "stepper_residual",
+               allow_soft=True)
+        return r.value
+
+    def sfd_baseflow(self, omega, chi: float, Delta: float, tol: float, max_steps: int, check_every: int = 100):
+        r = ctypes.c_double()
+        steps = ctypes.c_long()
+        rc = _check(self._lib.sfd_baseflow(self._h, self._p(omega, "omega"), float(chi), float(Delta), float(tol),
+                                           int(max_steps), int(check_every), ctypes.byref(r), ctypes.byref(steps)),
+                    "sfd_baseflow", allow_soft=True)
+        return rc, r.value, steps.value
+
+    def arnoldi_eigs(self, base, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
+                     eigvecs=None) -> EigResult:
+        re, im, res = np.zeros(nev + 1), np.zeros(nev + 1), np.zeros(nev + 1)
+        n_eig, n_conv, n_mv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        bp = self._p(base, "base") if base is not None else None
+        ev = None
+        if eigvecs is not None:
+            if eigvecs.shape[0] < nev + 1:
+                raise ValueError("eigvecs must hold nev + 1 fields")
+            ev = _field_ptr(eigvecs, self.shape, "eigvecs")
+        rc = _check(self._lib.arnoldi_eigs(self._h, bp, self._p(v0, "v0"), int(m), int(nev), float(tol),
+                                           int(max_restarts), float(T), re.ctypes.data_as(_dp),
+                                           im.ctypes.data_as(_dp), res.ctypes.data_as(_dp), ev,
+                                           ctypes.byref(n_eig), ctypes.byref(n_conv), ctypes.byref(n_mv)),
+                    "arnoldi_eigs", allow_soft=True)
+        k = n_eig.value
+        return EigResult(re[:k] + 1j * im[:k], res[:k], n_conv.value, n_mv.value, rc)
+
+    KERNELS = ("col_poisson", "row_inverse_psi", "row_forward_rhs", "col_update", "row_inverse_star",
+               "row_forward_pen")
+
+    def stepper_profile_linear(self, v, nsteps: int) -> dict:
+        """Per-kernel milliseconds (summed over nsteps linearised steps)."""
+        ms = np.zeros(6)
+        _check(self._lib.stepper_profile_linear(self._h, self._p(v, "v"), int(nsteps), ms.ctypes.data_as(_dp)),
+               "stepper_profile_linear")
+        return dict(zip(self.KERNELS, ms.tolist()))
+
+    def steps_for(self, T: float) -> int:
+        k = int(round(T / self.cfg.dt))
+        if k < 1 or not math.isclose(k * self.cfg.dt, T, rel_tol=1e-9):
+            raise ValueError("T must be a whole number of steps")
+        return k

@@ -1,0 +1,117 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every symbol that
+include/nsstab.h declares, validates arguments before touching a GPU, and its
+host dense eigen-solver (the Ritz-value / Schur step of the Krylov layer)
+agrees with LAPACK.  No compute call here needs a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+from paper_1804_03859_gb300 import build, nsstab
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return nsstab.load_library()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "nsstab.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?(?:void|int|char)\s*\*?\s*(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert sorted(n for n, _, _ in nsstab.SIGNATURES) == names
+
+
+def test_config_defaults_match_the_cylinder_case(lib):
+    from oracle import ns2d
+
+    cfg = nsstab.config_default()
+    ref = ns2d.Config()
+    for k in ("nx", "ny", "Lx", "Ly", "dt", "Re", "Uinf", "cyl_x", "cyl_y", "cyl_D", "eta", "mask_cells",
+              "sponge_frac", "sponge_sigma"):
+        assert getattr(cfg, k) == getattr(ref, k), k
+    assert cfg.precision == 64
+
+
+@pytest.mark.parametrize("field,value", [("nx", 100), ("ny", 4), ("nx", 8192), ("dt", 0.0), ("Re", -1.0),
+                                         ("precision", 16), ("eta", 0.0)])
+def test_bad_configs_are_rejected_before_any_device_call(lib, field, value):
+    cfg = nsstab.config_default()
+    setattr(cfg, field, value)
+    h = ctypes.c_void_p()
+    rc = lib.stepper_create(ctypes.byref(cfg), None, ctypes.byref(h))
+    assert rc == -1
+    assert h.value is None
+    assert len(lib.nsstab_last_error()) > 0
+
+
+def test_null_arguments_are_rejected(lib):
+    assert lib.step_nonlinear(None, None, 1) == -1
+    assert lib.apply_expTL(None, None, None, None, 1.0) == -1
+    assert lib.cgs2_orthogonalize(None, 1, 1, 1, None, None, None, None) == -1
+
+
+def _match(a, b):
+    return max(np.min(np.abs(b - x)) for x in a)
+
+
+@pytest.mark.parametrize("n,seed", [(5, 0), (24, 1), (80, 2), (150, 3)])
+def test_dense_eig_matches_lapack(lib, n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    w, V = nsstab.dense_eig(A)
+    wl = np.linalg.eigvals(A)
+    scale = np.abs(wl).max()
+    assert _match(w, wl) < 1e-10 * scale and _match(wl, w) < 1e-10 * scale
+    for k in range(n):
+        v = V[:, k]
+        assert abs(np.linalg.norm(v) - 1) < 1e-12
+        assert np.linalg.norm(A @ v - w[k] * v) < 1e-9 * scale
+
+
+def test_dense_eig_on_hessenberg_input_and_repeated_values(lib):
+    rng = np.random.default_rng(5)
+    H = np.triu(rng.standard_normal((40, 40)), -1)
+    w = nsstab.dense_eig(H, is_hessenberg=True, vectors=False)
+    assert _match(w, np.linalg.eigvals(H)) < 1e-10 * np.abs(w).max()
+    # a rotation-like matrix with conjugate pairs of equal modulus
+    B = scipy.linalg.block_diag(*[np.array([[np.cos(t), -np.sin(t)], [np.sin(t), np.cos(t)]]) * r
+                                  for t, r in [(0.3, 1.0), (1.1, 0.9), (2.0, 0.5)]])
+    Q, _ = np.linalg.qr(rng.standard_normal((6, 6)))
+    w = nsstab.dense_eig(Q @ B @ Q.T, vectors=False)
+    assert _match(w, np.linalg.eigvals(B)) < 1e-12
+
+
+@pytest.mark.parametrize("n,seed", [(12, 0), (40, 1), (100, 2)])
+def test_ordered_schur_puts_the_wanted_values_first(lib, n, seed):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) / np.sqrt(n)
+    mags = np.sort(np.abs(np.linalg.eigvals(A)))[::-1]
+    thr = 0.5 * (mags[n // 3] + mags[n // 3 + 1])
+    T, Z, p = nsstab.dense_schur_ordered(A, thr)
+    assert np.abs(Z.T @ Z - np.eye(n)).max() < 1e-12
+    assert np.linalg.norm(Z @ T @ Z.T - A) < 1e-12 * np.linalg.norm(A)
+    assert np.abs(np.tril(T, -2)).max() == 0.0
+    lead = np.linalg.eigvals(T[:p, :p])
+    tail = np.linalg.eigvals(T[p:, p:])
+    assert np.all(np.abs(lead) >= thr) and np.all(np.abs(tail) < thr)
+    assert p == int(np.sum(mags >= thr))
+    # same invariant subspace as scipy's sorted Schur form
+    _, Zs, sdim = scipy.linalg.schur(A, output="real", sort=lambda x, y: np.hypot(x, y) >= thr)
+    assert sdim == p
+    s = np.linalg.svd(Z[:, :p].T @ Zs[:, :p], compute_uv=False)
+    assert s.min() > 1 - 1e-10

@@ -1,0 +1,152 @@
+"""GPU parity of the Krylov layer (steps a6-a7): CGS2 against numpy, Arnoldi
+and Krylov-Schur eigenvalues against the oracle's Arnoldi and against LAPACK
+on the explicitly assembled propagator.  Bar: leading eigenvalues within
+1e-8 (FP64 stepper) and 1e-5 relative (FP32 stepper)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import dense, krylov, ns2d  # noqa: E402
+from paper_1804_03859_gb300 import inputs, nsstab  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _match(a, b):
+    return max(np.min(np.abs(b - x)) for x in a)
+
+
+@pytest.mark.parametrize("n,j", [(1000, 0), (1000, 1), (8192, 7), (131072, 65), (100003, 129)])
+def test_cgs2_parity(n, j):
+    rng = np.random.default_rng(n + j)
+    V = np.linalg.qr(rng.standard_normal((n, max(j, 1))))[0][:, :j] if j else np.zeros((n, 0))
+    w = rng.standard_normal(n)
+    Vd = _dev(np.ascontiguousarray(V.T)) if j else torch.zeros(1, dtype=torch.float64, device="cuda")
+    wd = _dev(w)
+    h, beta = nsstab.cgs2_orthogonalize(Vd, n, j, wd)
+    torch.cuda.synchronize()
+    h1 = V.T @ w
+    w1 = w - V @ h1
+    h2 = V.T @ w1
+    w2 = w1 - V @ h2
+    assert np.allclose(h, h1 + h2, rtol=0, atol=1e-12 * np.linalg.norm(w))
+    assert abs(beta - np.linalg.norm(w2)) <= 1e-12 * np.linalg.norm(w)
+    got = wd.cpu().numpy()
+    assert np.linalg.norm(got - w2) <= 1e-12 * np.linalg.norm(w)
+    if j:
+        assert np.abs(V.T @ got).max() <= 1e-13 * np.linalg.norm(w)
+
+
+@pytest.fixture(scope="module")
+def small():
+    kw = dict(nx=32, ny=16, dt=0.02, Re=50.0)
+    cfg = ns2d.Config(**kw)
+    base = inputs.wake_like_field(16, 32, seed=7)
+    T = 2.0
+    M = dense.assemble_M(ns2d.Base.from_omega(base, cfg), T, cfg)
+    mu = np.linalg.eigvals(M)
+    return kw, cfg, base, T, mu[krylov.leading_order(mu)]
+
+
+def test_arnoldi_matches_dense_eigendecomposition(small):
+    kw, cfg, base, T, mu_dense = small
+    st = nsstab.Stepper(**kw)
+    v0 = inputs.gaussian_field(16, 32, seed=11)
+    res = st.arnoldi_eigs(_dev(base), _dev(v0), m=150, nev=4, tol=1e-10, T=T)
+    assert res.status == nsstab.OK and res.n_conv == len(res.mu) == 5
+    assert res.n_matvec == 150
+    assert _match(res.mu, mu_dense[:6]) <= 1e-10
+
+
+def test_arnoldi_ritz_values_match_the_oracle_arnoldi(small):
+    kw, cfg, base, T, _ = small
+    b = ns2d.Base.from_omega(base, cfg)
+    v0 = inputs.gaussian_field(16, 32, seed=12)
+    m = 40
+    st = nsstab.Stepper(**kw)
+    got = st.arnoldi_eigs(_dev(base), _dev(v0), m=m, nev=6, tol=1e-6, T=T)
+    ref = krylov.arnoldi_eigs(lambda x: ns2d.apply_expTL(b, x.reshape(16, 32), T, cfg).ravel(),
+                              v0.ravel(), m=m, nev=6, tol=1e-6)
+    assert len(got.mu) == len(ref.mu)
+    assert _match(got.mu, ref.mu) <= 1e-8 and _match(ref.mu, got.mu) <= 1e-8
+    for g, r in zip(np.sort_complex(got.mu), np.sort_complex(ref.mu)):
+        pass
+    order_g = np.lexsort((-got.mu.imag, -np.abs(got.mu)))
+    assert np.all(order_g == np.arange(len(got.mu)))
+    # residual estimates agree where they are above round-off
+    assert np.allclose(np.sort(got.residual), np.sort(ref.residual), rtol=1e-5, atol=1e-12)
+
+
+def test_krylov_schur_matches_dense(small):
+    kw, cfg, base, T, mu_dense = small
+    st = nsstab.Stepper(**kw)
+    v0 = inputs.gaussian_field(16, 32, seed=14)
+    res = st.arnoldi_eigs(_dev(base), _dev(v0), m=40, nev=4, tol=1e-11, T=T, max_restarts=200)
+    assert res.status == nsstab.OK and res.n_conv == len(res.mu)
+    assert res.n_matvec > 40
+    assert _match(res.mu, mu_dense[:6]) <= 1e-10
+
+
+def test_ritz_vectors_are_eigenvectors(small):
+    kw, cfg, base, T, mu_dense = small
+    st = nsstab.Stepper(**kw)
+    v0 = inputs.gaussian_field(16, 32, seed=15)
+    vecs = torch.zeros(6, 16, 32, dtype=torch.float64, device="cuda")
+    res = st.arnoldi_eigs(_dev(base), _dev(v0), m=150, nev=3, tol=1e-10, T=T, eigvecs=vecs)
+    V = vecs.cpu().numpy().reshape(6, -1)
+    b = ns2d.Base.from_omega(base, cfg)
+    k = 0
+    while k < len(res.mu):
+        mu = res.mu[k]
+        if abs(mu.imag) > 0 and k + 1 < len(res.mu):
+            x = V[k] + 1j * V[k + 1]
+            step = 2
+        else:
+            x = V[k].astype(complex)
+            step = 1
+        Mx = ns2d.apply_expTL(b, x.real.reshape(16, 32), T, cfg) + 1j * ns2d.apply_expTL(b, x.imag.reshape(16, 32), T, cfg)
+        assert np.linalg.norm(Mx.ravel() - mu * x) <= 1e-9 * np.linalg.norm(x)
+        assert abs(np.linalg.norm(x) - 1) < 1e-10
+        k += step
+
+
+def test_cylinder_case_128x64_arnoldi_against_oracle():
+    """The 128x64 cylinder workload: Krylov dimension 64, leading 4 values."""
+    kw = dict(nx=128, ny=64, dt=0.01, Re=50.0)
+    cfg = ns2d.Config(**kw)
+    base = ns2d.step_nonlinear(np.zeros((64, 128)), 300, cfg)   # developing wake
+    v0 = inputs.gaussian_field(64, 128, seed=0)
+    T, m = 0.5, 64
+    st = nsstab.Stepper(**kw)
+    got = st.arnoldi_eigs(_dev(base), _dev(v0), m=m, nev=4, tol=1e-8, T=T)
+    b = ns2d.Base.from_omega(base, cfg)
+    ref = krylov.arnoldi_eigs(lambda x: ns2d.apply_expTL(b, x.reshape(64, 128), T, cfg).ravel(),
+                              v0.ravel(), m=m, nev=4, tol=1e-8)
+    assert len(got.mu) == len(ref.mu)
+    assert _match(got.mu, ref.mu) <= 1e-8
+
+
+def test_fp32_stepper_eigenvalues_within_1e5(small):
+    kw, cfg, base, T, mu_dense = small
+    st = nsstab.Stepper(precision=32, **kw)
+    v0 = inputs.gaussian_field(16, 32, seed=16)
+    res = st.arnoldi_eigs(_dev(base), _dev(v0), m=40, nev=4, tol=1e-6, T=T, max_restarts=200)
+    assert res.n_conv == len(res.mu)
+    for mu in res.mu:
+        assert np.min(np.abs(mu_dense - mu)) <= 1e-5 * abs(mu)
+
+
+def test_invalid_krylov_arguments():
+    st = nsstab.Stepper(nx=16, ny=8)
+    v0 = _dev(inputs.gaussian_field(8, 16, seed=1))
+    base = _dev(np.zeros((8, 16)))
+    for m, nev in [(1, 1), (200, 2), (10, 10)]:
+        with pytest.raises(nsstab.NsstabError):
+            st.arnoldi_eigs(base, v0, m=m, nev=nev, tol=1e-8, T=0.5)
+    with pytest.raises(nsstab.NsstabError):
+        st.arnoldi_eigs(base, torch.zeros(8, 16, dtype=torch.float64, device="cuda"), m=10, nev=2, tol=1e-8, T=0.5)
