@@ -60,6 +60,8 @@ SIGNATURES = [
     ("stepper_profile_linear", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _dp]),
     ("cgs2_orthogonalize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
                                           ctypes.c_void_p, _dp, _dp, ctypes.c_void_p]),
+    ("cgs2_orthogonalize_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
+                                                  ctypes.c_void_p, _dp, _dp, ctypes.c_void_p]),
     ("nsstab_dense_eig", ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp, _dp]),
     ("nsstab_dense_schur_ordered", ctypes.c_int, [ctypes.c_int, _dp, ctypes.c_double, _dp, _dp, _ip]),
     ("nsstab_last_error", ctypes.c_char_p, []),
@@ -155,6 +157,29 @@ def cgs2_orthogonalize(V, n: int, j: int, w, ldv: int | None = None, stream=None
     vp = ctypes.c_void_p(V.data_ptr()) if j > 0 else ctypes.c_void_p(0)
     _check(lib.cgs2_orthogonalize(vp, ldv if ldv is not None else n, n, j, ctypes.c_void_p(w.data_ptr()),
                                   h.ctypes.data_as(_dp), ctypes.byref(beta), s), "cgs2_orthogonalize")
+    return h[:j], beta.value
+
+
+NOALLOC_MAX_COLS = 256
+
+
+def cgs2_orthogonalize_noalloc(V, n: int, j: int, w, ldv: int | None = None, stream=None):
+    """cgs2_orthogonalize without any device allocation (fixed static scratch;
+    j <= NOALLOC_MAX_COLS).  For callers that cannot allocate at call time."""
+    import torch
+
+    lib = load_library()
+    if w.dtype != torch.float64 or w.device.type != "cuda" or not w.is_contiguous():
+        raise ValueError("w must be a contiguous float64 CUDA tensor")
+    if j > 0 and (V.dtype != torch.float64 or V.device.type != "cuda" or not V.is_contiguous()):
+        raise ValueError("V must be a contiguous float64 CUDA tensor")
+    h = np.zeros(max(j, 1))
+    beta = ctypes.c_double()
+    s = current_stream_handle() if stream is None else ctypes.c_void_p(stream)
+    vp = ctypes.c_void_p(V.data_ptr()) if j > 0 else ctypes.c_void_p(0)
+    _check(lib.cgs2_orthogonalize_noalloc(vp, ldv if ldv is not None else n, n, j, ctypes.c_void_p(w.data_ptr()),
+                                          h.ctypes.data_as(_dp), ctypes.byref(beta), s),
+           "cgs2_orthogonalize_noalloc")
     return h[:j], beta.value
 
 
