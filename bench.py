@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--impl", choices=("native", "reference"), default="native")
     ap.add_argument("--no-eigs", action="store_true", help="skip the time-to-eigenvalues legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch plans (skip the autotuner)")
     return ap.parse_args()
 
 
@@ -256,8 +257,13 @@ def run_native(args, rank: int, world: int):
     base = torch.from_numpy(inputs.wake_like_field(NY, NX, seed=0)).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    plans = {}
+
     def make(prec):
         st = nsstab.Stepper(nx=NX, ny=NY, dt=DT, Re=RE, precision=prec)
+        if not args.no_tune:
+            st.stepper_autotune(reps=5)       # project autotuner: launch plan per kernel
+        plans[f"fp{prec}"] = st.plans()
         st.stepper_set_base(base)
         return st
 
@@ -380,7 +386,8 @@ def run_native(args, rank: int, world: int):
                    "steps_per_matvec": nsteps, "krylov_m": KRYLOV_M, "cgs2_basis": BASIS_J,
                    "base_flow": "synthetic developed-wake field (not a converged steady state)",
                    "l2": "flushed (512 MiB write) before every timed step",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "launch_plans": plans},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": e2e,

@@ -174,6 +174,22 @@ int cgs2_orthogonalize_noalloc(const double* V, long ldv, long n, int j, double*
  * steps leave behind is discarded.  Synchronous. */
 int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, double* kernel_ms);
 
+/* Launch plans of the six step kernels (ids 0..5 in the order of
+ * stepper_profile_linear).  A plan is (log2_elems, per_block): each thread
+ * of the FFT passes owns 2^log2_elems elements (1, 2 or 3), and a block
+ * handles per_block row pairs or columns (a power of two).  Plans change
+ * the launch shape and the radix of the transforms, not the method; results
+ * agree to rounding.  stepper_create picks a default from the grid size.
+ * stepper_autotune times every valid plan of each kernel (reps launches
+ * each) and keeps the fastest; it overwrites the stepper's workspace (not
+ * its base flow) and, if plans is not NULL, stores the chosen
+ * (log2_elems, per_block) of kernel k in plans[2k], plans[2k+1] (host, 12
+ * ints).  stepper_set_plan rejects a plan that does not fit the grid
+ * (INVALID_ARG).  All synchronous. */
+int stepper_autotune(nsstab_stepper* st, int reps, int* plans);
+int stepper_set_plan(nsstab_stepper* st, int kernel, int log2_elems, int per_block);
+int stepper_get_plan(nsstab_stepper* st, int kernel, int* log2_elems, int* per_block);
+
 /* One CGS2 orthogonalisation (Algorithm 1's Gram-Schmidt step applied
  * twice): h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2;
  * beta = ||w||.  V: device, j columns of length n with leading dimension

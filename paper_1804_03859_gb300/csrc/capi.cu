@@ -184,6 +184,23 @@ int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, doub
     return st->impl->profile_linear(v, nsteps, kernel_ms);
 }
 
+int stepper_autotune(nsstab_stepper* st, int reps, int* plans) {
+    if (!st || reps < 1 || reps > 1000) return bad_arg("stepper_autotune: bad argument");
+    return st->impl->autotune(reps, plans);
+}
+
+int stepper_set_plan(nsstab_stepper* st, int kernel, int log2_elems, int per_block) {
+    if (!st) return bad_arg("stepper_set_plan: null stepper");
+    return st->impl->set_plan(kernel, log2_elems, per_block);
+}
+
+int stepper_get_plan(nsstab_stepper* st, int kernel, int* log2_elems, int* per_block) {
+    if (!st || !log2_elems || !per_block) return bad_arg("stepper_get_plan: null argument");
+    const int rc = st->impl->plan_of(kernel, log2_elems, per_block);
+    if (rc != NSSTAB_OK) return bad_arg("stepper_get_plan: kernel must be in [0, 6)");
+    return NSSTAB_OK;
+}
+
 int cgs2_orthogonalize(const double* V, long ldv, long n, int j, double* w, double* h, double* beta, void* stream) {
     if (!w || !beta || (j > 0 && (!V || !h))) return bad_arg("cgs2_orthogonalize: null argument");
     if (n < 1 || j < 0 || j > 4096 || (j > 0 && ldv < n)) return bad_arg("cgs2_orthogonalize: bad sizes");

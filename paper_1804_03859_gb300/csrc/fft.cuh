@@ -1,10 +1,13 @@
 // Shared-memory Stockham FFT for the row and column passes of the stepper.
 //
-// A block transforms `nseq` complex sequences of length N = 2^logN (N >= 8)
-// in place in shared memory.  Every thread owns 8 elements per pass:
-// radix-8 passes while at least three factors of two remain, then one
-// radix-4 (two butterflies per thread) or radix-2 (four butterflies per
-// thread) pass.  The Stockham (self-sorting) index map is used, so input and
+// A block transforms `nseq` complex sequences of length N = 2^logN in place
+// in shared memory.  Every thread owns E = 2, 4 or 8 elements per pass
+// (template parameter): radix-E passes while enough factors of two remain,
+// then one smaller-radix pass with several butterflies per thread.  Fewer
+// elements per thread means more warps for the same transform, which is
+// what small grids need to occupy all four SM sub-partitions (on GB300 a
+// warp-wide FP64 instruction holds a sub-partition's FP64 unit for 64
+// cycles, so each sub-partition needs its own warp).  The Stockham (self-sorting) index map is used, so input and
 // output are both in natural order and no bit reversal is needed.
 //
 // Shared-memory layout: sequence f occupies S = padded_len(N) (or more)
@@ -68,98 +71,77 @@ __device__ __forceinline__ Cx<T> twiddle(Cx<T> a, const Cx<T>* __restrict__ tw, 
     return INV ? cmulc(a, w) : cmul(a, w);
 }
 
+template <bool INV, class T, int LR> __device__ __forceinline__ void dft_r(Cx<T>* v) {
+    if (LR == 3) {
+        dft8<INV, T>(v);
+    } else if (LR == 2) {
+        dft4<INV>(v[0], v[1], v[2], v[3]);
+    } else {
+        const Cx<T> a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    }
+}
+
+// One Stockham pass of radix R = 2^LR for a thread owning E = 2^LE elements
+// (E/R butterflies).  Butterfly b reads b + r N/R and writes
+// (b - k) R + k + r Ns with k = b mod Ns, after twiddling input r by
+// W_N^(r k N/(Ns R)).
+template <bool INV, class T, int LE, int LR>
+__device__ __forceinline__ void stockham_pass(Cx<T>* d, int q, int lq, int logN, int nsl,
+                                              const Cx<T>* __restrict__ tw, int twshift, bool act) {
+    constexpr int E = 1 << LE, R = 1 << LR, U = E / R;
+    Cx<T> v[E];
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[u * R + r] = d[pad8(q + (u << lq) + (r << (logN - LR)))];
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int b = q + (u << lq);
+            const int k = b & ((1 << nsl) - 1);
+            if (nsl > 0) {
+                const int sh = logN - nsl - LR + twshift;
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[u * R + r] = twiddle<INV, T>(v[u * R + r], tw, (r * k) << sh);
+            }
+            dft_r<INV, T, LR>(v + u * R);
+            const int base = ((b - k) << LR) + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[pad8(base + (r << nsl))] = v[u * R + r];
+        }
+    }
+    __syncthreads();
+}
+
 // In-place transform of nseq sequences (see file comment).  All threads of
-// the block must call it.  Requirements: blockDim.x * 8 is a multiple of N;
-// twshift = log2(Nt / N) for the table tw of length Nt.
-template <bool INV, class T>
+// the block must call it.  Every thread owns E = 2^LE elements per pass:
+// radix-E passes, then one smaller radix for the remaining factors.
+// Requirements: logN >= LE; blockDim.x * E is a multiple of N; twshift =
+// log2(Nt / N) for the table tw of length Nt.
+template <bool INV, class T, int LE>
 __device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __restrict__ tw, int twshift) {
-    using C = Cx<T>;
     const int t = threadIdx.x;
-    const int lq = logN - 3;                    // log2(N/8): threads per sequence
+    const int lq = logN - LE;                   // log2(N/E): threads per sequence
     const int q = t & ((1 << lq) - 1);
     const int F = blockDim.x >> lq;             // sequences per round
     for (int f0 = 0; f0 < nseq; f0 += F) {
         const int f = f0 + (t >> lq);
         const bool act = f < nseq;
-        C* d = s + (size_t)(act ? f : 0) * S;
-        int nsl = 0;                            // log2 of the Stockham stride Ns
+        Cx<T>* d = s + (size_t)(act ? f : 0) * S;
+        int nsl = 0;
         int rem = logN;
-        while (rem > 0) {
-            C v[8];
-            if (rem >= 3) {                     // ---- radix 8
-                if (act) {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) v[r] = d[pad8(q + (r << lq))];
-                }
-                __syncthreads();
-                if (act) {
-                    const int k = q & ((1 << nsl) - 1);
-                    if (nsl > 0) {
-                        const int sh = logN - nsl - 3 + twshift;
-#pragma unroll
-                        for (int r = 1; r < 8; ++r) v[r] = twiddle<INV, T>(v[r], tw, (r * k) << sh);
-                    }
-                    dft8<INV, T>(v);
-                    const int base = ((q - k) << 3) + k;
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) d[pad8(base + (r << nsl))] = v[r];
-                }
-                __syncthreads();
-                nsl += 3;
-                rem -= 3;
-            } else if (rem == 2) {              // ---- radix 4, two butterflies
-                if (act) {
-#pragma unroll
-                    for (int u = 0; u < 2; ++u)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) v[4 * u + r] = d[pad8(q + (u << lq) + (r << (logN - 2)))];
-                }
-                __syncthreads();
-                if (act) {
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int b = q + (u << lq);
-                        const int k = b & ((1 << nsl) - 1);
-                        if (nsl > 0) {
-                            const int sh = logN - nsl - 2 + twshift;
-#pragma unroll
-                            for (int r = 1; r < 4; ++r) v[4 * u + r] = twiddle<INV, T>(v[4 * u + r], tw, (r * k) << sh);
-                        }
-                        dft4<INV>(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
-                        const int base = ((b - k) << 2) + k;
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) d[pad8(base + (r << nsl))] = v[4 * u + r];
-                    }
-                }
-                __syncthreads();
-                nsl += 2;
-                rem = 0;
-            } else {                            // ---- radix 2, four butterflies
-                if (act) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        v[2 * u] = d[pad8(q + (u << lq))];
-                        v[2 * u + 1] = d[pad8(q + (u << lq) + (1 << (logN - 1)))];
-                    }
-                }
-                __syncthreads();
-                if (act) {
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        const int b = q + (u << lq);
-                        const int k = b & ((1 << nsl) - 1);
-                        if (nsl > 0) v[2 * u + 1] = twiddle<INV, T>(v[2 * u + 1], tw, k << (logN - nsl - 1 + twshift));
-                        const C x0 = v[2 * u], x1 = v[2 * u + 1];
-                        const int base = ((b - k) << 1) + k;
-                        d[pad8(base)] = cadd(x0, x1);
-                        d[pad8(base + (1 << nsl))] = csub(x0, x1);
-                    }
-                }
-                __syncthreads();
-                nsl += 1;
-                rem = 0;
-            }
+        while (rem >= LE) {
+            stockham_pass<INV, T, LE, LE>(d, q, lq, logN, nsl, tw, twshift, act);
+            nsl += LE;
+            rem -= LE;
         }
+        if (LE == 3 && rem == 2) stockham_pass<INV, T, LE, (LE == 3 ? 2 : 1)>(d, q, lq, logN, nsl, tw, twshift, act);
+        if (rem == 1) stockham_pass<INV, T, LE, 1>(d, q, lq, logN, nsl, tw, twshift, act);
     }
 }
 

@@ -20,8 +20,10 @@
 // .x and X[nx/2] (real) in .y.  In the column passes the packed kx = 0
 // column is the y-transform of (X0 + i XN); the spectral operators act on it
 // through its Hermitian halves (see apply_packed0).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "fft.cuh"
@@ -112,7 +114,7 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
 
 // Forward x-transform of RP row pairs per block, with the row values made by
 // MODE.  Writes the packed half-spectra to X1 ([kx][y]) when do_fft.
-template <class T, int MODE>
+template <class T, int MODE, int LE>
 __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
     using C = Cx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -128,7 +130,7 @@ __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_
     }
     if (!do_fft) return;
     __syncthreads();
-    fft_smem<false, T>(s, f.logx, S, RP, f.twx, 0);
+    fft_smem<false, T, LE>(s, f.logx, S, RP, f.twx, 0);
     // split Z = FFT(a + i b) into the half-spectra of a and b
     const int nh = nx >> 1;
     for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
@@ -155,7 +157,7 @@ __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_
 // Inverse x-transform of RP row pairs per block.  same: pair p = rows
 // (2p, 2p+1) of XA -> dA; otherwise pair p = row p of XA -> dA and row p of
 // XB -> dB.
-template <class T>
+template <class T, int LE>
 __global__ void k_row_inverse(Fields<T> f, const Cx<T>* __restrict__ XA, const Cx<T>* __restrict__ XB,
                               T* dA, T* dB, int RP, int logRP, bool same) {
     using C = Cx<T>;
@@ -180,7 +182,7 @@ __global__ void k_row_inverse(Fields<T> f, const Cx<T>* __restrict__ XA, const C
         }
     }
     __syncthreads();
-    fft_smem<true, T>(s, f.logx, S, RP, f.twx, 0);
+    fft_smem<true, T, LE>(s, f.logx, S, RP, f.twx, 0);
     for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
         const int p = e >> f.logx, i = e & (nx - 1);
         const int pr = pair0 + p;
@@ -204,7 +206,7 @@ __device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
 
 // Forward y-transform of CP columns of X1, store Wh, psi^ = scale * tP * omega^,
 // inverse y-transform into X2.
-template <class T>
+template <class T, int LE>
 __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
     using C = Cx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -216,7 +218,7 @@ __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
         s[c * S + pad8(j)] = f.X1[(size_t)(c0 + c) * ny + j];
     }
     __syncthreads();
-    fft_smem<false, T>(s, logy, S, CP, f.twy, 0);
+    fft_smem<false, T, LE>(s, logy, S, CP, f.twy, 0);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, k = e & (ny - 1);
         f.Wh[(size_t)(c0 + c) * ny + k] = s[c * S + pad8(k)];
@@ -237,7 +239,7 @@ __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
         }
     }
     __syncthreads();
-    fft_smem<true, T>(s, logy, S, CP, f.twy, 0);
+    fft_smem<true, T, LE>(s, logy, S, CP, f.twy, 0);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
         f.X2[(size_t)(c0 + c) * ny + j] = s[c * S + pad8(j)];
@@ -248,7 +250,7 @@ __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
 //   omega*^ = tA omega^ + tB (c1 N^n + c0 N^{n-1}),  psi*^ = tP omega*^
 // (tA, tB carry the 1/(nx ny) of the inverse transform); Nh <- N^n; inverse
 // y-transforms of omega*^ -> X1 and psi*^ -> X2.
-template <class T>
+template <class T, int LE>
 __global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
     using C = Cx<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -261,7 +263,7 @@ __global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
         s1[c * S + pad8(j)] = f.X1[(size_t)(c0i + c) * ny + j];
     }
     __syncthreads();
-    fft_smem<false, T>(s1, logy, S, CP, f.twy, 0);
+    fft_smem<false, T, LE>(s1, logy, S, CP, f.twy, 0);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, k = e & (ny - 1);
         const int kx = c0i + c;
@@ -296,7 +298,7 @@ __global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
         }
     }
     __syncthreads();
-    fft_smem<true, T>(s1, logy, S, 2 * CP, f.twy, 0);
+    fft_smem<true, T, LE>(s1, logy, S, 2 * CP, f.twy, 0);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
         const size_t g = (size_t)(c0i + c) * ny + j;
@@ -351,13 +353,22 @@ __global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, s
 
 // ------------------------------------------------------------- host side
 
+// One launch configuration: `per` sequences (row pairs or columns) per
+// block, 2^le elements per thread in the FFT passes.
 struct Launch {
-    int blocks = 0, threads = 0, per = 0, logper = 0;
+    int blocks = 0, threads = 0, per = 0, logper = 0, le = 3;
     size_t smem = 0;
+    bool ok = false;
 };
+
+// the six kernels of a step, in order
+enum KernelId { KCOLP = 0, KINVP = 1, KFWDR = 2, KCOLU = 3, KINVR = 4, KFWDP = 5 };
+template <class T> int max_threads_for(int kid, int le);
 
 static const int kRedBlocks = 256;
 static const double kPi = 3.14159265358979323846;
+static const int kGraphChunk = 256;         // time steps per captured graph
+static const size_t kMaxSmem = 200 * 1024;
 
 template <class T>
 class StepperImpl : public StepperBase {
@@ -376,10 +387,19 @@ class StepperImpl : public StepperBase {
             double* r, long* steps) override;
     int launches_per_step() const override { return kNumStepKernels; }
     int profile_linear(const double* v, int nsteps, double* ms) override;
+    int autotune(int reps, int* chosen) override;
+    int plan_of(int kid, int* le, int* per) const override {
+        if (kid < 0 || kid >= kNumStepKernels) return NSSTAB_ERR_INVALID_ARG;
+        *le = plan_[kid].le;
+        *per = plan_[kid].per;
+        return NSSTAB_OK;
+    }
+    int set_plan(int kid, int le, int per) override;
 
   private:
     nsstab_config cfg_;
     cudaStream_t stream_;
+    cudaStream_t cap_ = nullptr;   // private stream used only to capture graphs
     Fields<T> f_{};
     int nx_ = 0, ny_ = 0, nxh_ = 0;
     size_t n_ = 0;
@@ -389,8 +409,13 @@ class StepperImpl : public StepperBase {
     double* red_ = nullptr;       // device partials
     double* red_host_ = nullptr;  // pinned
     bool have_base_ = false;
-    Launch lfwd_, linv_pairs_, linv_rows_, lcolp_, lcolu_;
+    Launch plan_[kNumStepKernels];
     T scale_ = T(1);
+    struct GraphKey {
+        int nsteps, flags;
+        bool operator<(const GraphKey& o) const { return nsteps != o.nsteps ? nsteps < o.nsteps : flags < o.flags; }
+    };
+    std::map<GraphKey, cudaGraphExec_t> graphs_;
 
     template <class P> int dalloc(P** p, size_t count) {
         void* q = nullptr;
@@ -403,57 +428,223 @@ class StepperImpl : public StepperBase {
         *p = static_cast<P*>(q);
         return NSSTAB_OK;
     }
+    void clear_graphs() {
+        for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second);
+        graphs_.clear();
+    }
     void release() {
         cudaStreamSynchronize(stream_);
+        clear_graphs();
+        if (cap_) cudaStreamDestroy(cap_);
+        cap_ = nullptr;
         for (void* p : allocs_) cudaFree(p);
         allocs_.clear();
         if (red_host_) cudaFreeHost(red_host_);
         red_host_ = nullptr;
     }
     int build_tables();
-    Launch plan_rows(int npairs, size_t per_seq_bytes);
-    Launch plan_cols(int nseq_per_col, size_t per_seq_bytes);
+    Launch make_plan(int kid, int le, int per) const;
+    Launch default_plan(int kid) const;
+    int set_smem_attr(int kid, const Launch& L);
 
+    int launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first);
+    int launch_plain(cudaStream_t st);
     int load(const double* src, T* dst);
     int store(const T* src, double* dst);
     int transform_W();                                   // X1 = x-spectrum of W
-    int stream_function();                               // Wh, X2, P from X1
-    int run_steps(int nsteps, bool linear, bool sfd, bool fft_last);
+    int stream_function(cudaStream_t st);                // Wh, X2, P from X1
+    int issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last);
+    int run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1 = true);
     int sumsq_diff(const T* a, const T* b, double* out);
+    int time_kernel(int kid, const Launch& L, int reps, float* ms);
 };
 
-template <class T> Launch StepperImpl<T>::plan_rows(int npairs, size_t per_seq_bytes) {
-    // pairs per block: at least one warp of threads, then grow while enough
-    // blocks remain to fill the GPU twice over
-    const int per = nx_ / 8;
-    int rp = 1;
-    while (rp * per < 32 && 2 * rp <= npairs) rp *= 2;
-    while (2 * rp <= npairs && npairs / (2 * rp) >= 304 && 2 * rp * per <= 256 && 2 * rp * per_seq_bytes <= 96 * 1024)
-        rp *= 2;
+// ---------------------------------------------------------- launch plans
+
+template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) const {
     Launch L;
-    L.per = rp;
-    L.logper = ilog2(rp);
-    L.blocks = npairs / rp;
-    L.threads = rp * per;
-    L.smem = rp * per_seq_bytes;
+    const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
+    const int N = row ? nx_ : ny_;
+    const int logN = row ? ilog2(nx_) : ilog2(ny_);
+    const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;   // sequences of the launch
+    const int nseq_smem = (kid == KCOLU) ? 2 : 1;                     // smem sequences per unit
+    if (le < 1 || le > 3 || logN < le || per < 1 || !is_pow2(per) || per > count) return L;
+    const int threads = per * (N >> le);
+    const size_t smem = (size_t)per * nseq_smem * padded_len(N) * sizeof(C);
+    if (threads > 1024 || smem > kMaxSmem) return L;
+    L.per = per;
+    L.logper = ilog2(per);
+    L.le = le;
+    L.blocks = count / per;
+    L.threads = threads;
+    L.smem = smem;
+    L.ok = true;
     return L;
 }
 
-template <class T> Launch StepperImpl<T>::plan_cols(int nseq_per_col, size_t per_seq_bytes) {
-    const int per = ny_ / 8;
-    const int ncol = nxh_;
-    int cp = 1;
-    while (cp * per < 32 && 2 * cp <= ncol) cp *= 2;
-    while (2 * cp <= ncol && ncol / (2 * cp) >= 304 && 2 * cp * per <= 256 &&
-           2 * cp * nseq_per_col * per_seq_bytes <= 96 * 1024)
-        cp *= 2;
-    Launch L;
-    L.per = cp;
-    L.logper = ilog2(cp);
-    L.blocks = ncol / cp;
-    L.threads = cp * per;
-    L.smem = (size_t)cp * nseq_per_col * per_seq_bytes;
+// Default: the largest elements-per-thread (fewest FP64 operations per
+// point) that still gives every SM sub-partition a warp, then enough
+// sequences per block for at least two warps.
+template <class T> Launch StepperImpl<T>::default_plan(int kid) const {
+    const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
+    const int N = row ? nx_ : ny_;
+    const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;
+    const long target = 4L * 152 * 32;   // one warp per SM sub-partition
+    int le = 3;
+    while (le > 2 && (long)count * (N >> le) < target) --le;
+    if (ilog2(N) < le) le = ilog2(N);
+    int per = 1;
+    while (per * (N >> le) < 64 && 2 * per <= count) per *= 2;
+    Launch L = make_plan(kid, le, per);
+    while ((!L.ok || L.threads > max_threads_for<T>(kid, le)) && per > 1) L = make_plan(kid, le, per /= 2);
+    while ((!L.ok || L.threads > max_threads_for<T>(kid, le)) && le > 1) L = make_plan(kid, --le, 1);
     return L;
+}
+
+template <class T> int StepperImpl<T>::set_smem_attr(int kid, const Launch& L) {
+    const int sm = (int)L.smem;
+#define NS_ATTR(fn) NS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))
+#define NS_ATTR_LE(KERNEL)                 \
+    switch (L.le) {                        \
+        case 1: NS_ATTR(KERNEL(1)); break; \
+        case 2: NS_ATTR(KERNEL(2)); break; \
+        default: NS_ATTR(KERNEL(3)); break; \
+    }
+#define K_FWD_PLAIN(le) k_row_forward<T, FWD_PLAIN, le>
+#define K_FWD_RNL(le) k_row_forward<T, FWD_RHS_NL, le>
+#define K_FWD_RLIN(le) k_row_forward<T, FWD_RHS_LIN, le>
+#define K_FWD_PNL(le) k_row_forward<T, FWD_PEN_NL, le>
+#define K_FWD_PLIN(le) k_row_forward<T, FWD_PEN_LIN, le>
+#define K_INV(le) k_row_inverse<T, le>
+#define K_COLP(le) k_col_poisson<T, le>
+#define K_COLU(le) k_col_update<T, le>
+    switch (kid) {
+        case KCOLP: NS_ATTR_LE(K_COLP); break;
+        case KINVP:
+        case KINVR: NS_ATTR_LE(K_INV); break;
+        case KFWDR: NS_ATTR_LE(K_FWD_RNL); NS_ATTR_LE(K_FWD_RLIN); NS_ATTR_LE(K_FWD_PLAIN); break;
+        case KCOLU: NS_ATTR_LE(K_COLU); break;
+        default: NS_ATTR_LE(K_FWD_PNL); NS_ATTR_LE(K_FWD_PLIN); break;
+    }
+    return NSSTAB_OK;
+}
+
+// Largest block the register budget of the kernel instantiations behind
+// launch `kid` with 2^le elements per thread allows.
+template <class T> int max_threads_for(int kid, int le) {
+    cudaFuncAttributes a;
+    int m = 1024;
+    auto take = [&](const void* fn) {
+        if (cudaFuncGetAttributes(&a, fn) == cudaSuccess) m = std::min(m, a.maxThreadsPerBlock);
+        else m = 0;
+    };
+#define NS_TAKE_LE(KERNEL)                                  \
+    switch (le) {                                           \
+        case 1: take((const void*)KERNEL(1)); break;        \
+        case 2: take((const void*)KERNEL(2)); break;        \
+        default: take((const void*)KERNEL(3)); break;       \
+    }
+    switch (kid) {
+        case KCOLP: NS_TAKE_LE(K_COLP); break;
+        case KINVP:
+        case KINVR: NS_TAKE_LE(K_INV); break;
+        case KFWDR: NS_TAKE_LE(K_FWD_RNL); NS_TAKE_LE(K_FWD_RLIN); NS_TAKE_LE(K_FWD_PLAIN); break;
+        case KCOLU: NS_TAKE_LE(K_COLU); break;
+        default: NS_TAKE_LE(K_FWD_PNL); NS_TAKE_LE(K_FWD_PLIN); break;
+    }
+    return m;
+}
+
+template <class T> int StepperImpl<T>::set_plan(int kid, int le, int per) {
+    if (kid < 0 || kid >= kNumStepKernels) {
+        set_error("set_plan: bad kernel id");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    const Launch L = make_plan(kid, le, per);
+    if (!L.ok || L.threads > max_threads_for<T>(kid, le)) {
+        set_error("set_plan: configuration not valid for this grid");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    // the inverse-row kernel is shared by two launches: keep the larger smem attribute
+    NS_TRY(set_smem_attr(kid, L));
+    if (kid == KINVP || kid == KINVR) {
+        const Launch& o = plan_[kid == KINVP ? KINVR : KINVP];
+        if (o.ok && o.le == L.le && o.smem > L.smem) NS_TRY(set_smem_attr(kid, o));
+    }
+    plan_[kid] = L;
+    clear_graphs();
+    return NSSTAB_OK;
+}
+
+#define NS_DISPATCH_LE(L, CALL)  \
+    switch ((L).le) {            \
+        case 1: CALL(1); break;  \
+        case 2: CALL(2); break;  \
+        default: CALL(3); break; \
+    }
+
+template <class T> int StepperImpl<T>::launch_plain(cudaStream_t st) {
+    const Launch& L = plan_[KFWDR];
+#define CALL_PLAIN(le) \
+    k_row_forward<T, FWD_PLAIN, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+    NS_DISPATCH_LE(L, CALL_PLAIN);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first) {
+    const Launch& L = plan_[kid];
+    switch (kid) {
+        case KCOLP: {
+#define CALL_COLP(le) k_col_poisson<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, scale_)
+            NS_DISPATCH_LE(L, CALL_COLP);
+            break;
+        }
+        case KINVP: {
+#define CALL_INVP(le) \
+    k_row_inverse<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, f_.X2, f_.X2, f_.P, f_.P, L.per, L.logper, true)
+            NS_DISPATCH_LE(L, CALL_INVP);
+            break;
+        }
+        case KFWDR: {
+#define CALL_FRL(le) \
+    k_row_forward<T, FWD_RHS_LIN, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+#define CALL_FRN(le) \
+    k_row_forward<T, FWD_RHS_NL, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+            if (linear) {
+                NS_DISPATCH_LE(L, CALL_FRL);
+            } else {
+                NS_DISPATCH_LE(L, CALL_FRN);
+            }
+            break;
+        }
+        case KCOLU: {
+            const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
+#define CALL_COLU(le) k_col_update<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, c1, c0, first)
+            NS_DISPATCH_LE(L, CALL_COLU);
+            break;
+        }
+        case KINVR: {
+#define CALL_INVR(le) \
+    k_row_inverse<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, f_.X1, f_.X2, f_.W, f_.P, L.per, L.logper, false)
+            NS_DISPATCH_LE(L, CALL_INVR);
+            break;
+        }
+        default: {
+#define CALL_FPL(le) \
+    k_row_forward<T, FWD_PEN_LIN, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
+#define CALL_FPN(le) \
+    k_row_forward<T, FWD_PEN_NL, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
+            if (linear) {
+                NS_DISPATCH_LE(L, CALL_FPL);
+            } else {
+                NS_DISPATCH_LE(L, CALL_FPN);
+            }
+            break;
+        }
+    }
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
 }
 
 template <class T> int StepperImpl<T>::build_tables() {
@@ -577,26 +768,23 @@ template <class T> int StepperImpl<T>::init() {
     f_.Ub = f_.Vb = f_.DxOb = f_.DyOb = nullptr;
     NS_TRY(build_tables());
 
-    const size_t sx = padded_len(nx_) * sizeof(C), sy = padded_len(ny_) * sizeof(C);
-    lfwd_ = plan_rows(ny_ / 2, sx);
-    linv_pairs_ = plan_rows(ny_ / 2, sx);
-    linv_rows_ = plan_rows(ny_, sx);
-    lcolp_ = plan_cols(1, sy);
-    lcolu_ = plan_cols(2, sy);
-    const size_t big = 200 * 1024;
-    if (lfwd_.smem > big || linv_rows_.smem > big || lcolu_.smem > big) {
-        set_error("grid too large for the shared-memory FFT");
-        return NSSTAB_ERR_INVALID_ARG;
+    // zero the workspace so that timing runs of the autotuner see finite data
+    NS_CUDA(cudaMemsetAsync(f_.W, 0, n_ * sizeof(T), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.P, 0, n_ * sizeof(T), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.X1, 0, nc * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.X2, 0, nc * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.Wh, 0, nc * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.Nh, 0, nc * sizeof(C), stream_));
+    NS_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
+    for (int k = 0; k < kNumStepKernels; ++k) {
+        const Launch L = default_plan(k);
+        if (!L.ok) {
+            set_error("grid too large for the shared-memory FFT");
+            return NSSTAB_ERR_INVALID_ARG;
+        }
+        NS_TRY(set_plan(k, L.le, L.per));
     }
-    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_PLAIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
-    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_RHS_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
-    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_RHS_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
-    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_PEN_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
-    NS_CUDA(cudaFuncSetAttribute(k_row_forward<T, FWD_PEN_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lfwd_.smem));
-    const size_t inv_smem = linv_rows_.smem > linv_pairs_.smem ? linv_rows_.smem : linv_pairs_.smem;
-    NS_CUDA(cudaFuncSetAttribute(k_row_inverse<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv_smem));
-    NS_CUDA(cudaFuncSetAttribute(k_col_poisson<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lcolp_.smem));
-    NS_CUDA(cudaFuncSetAttribute(k_col_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lcolu_.smem));
+    NS_CUDA(cudaStreamSynchronize(stream_));
     return NSSTAB_OK;
 }
 
@@ -620,47 +808,120 @@ template <class T> int StepperImpl<T>::store(const T* src, double* dst) {
     return NSSTAB_OK;
 }
 
-template <class T> int StepperImpl<T>::transform_W() {
-    k_row_forward<T, FWD_PLAIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
-    NS_LAUNCH_CHECK();
+template <class T> int StepperImpl<T>::transform_W() { return launch_plain(stream_); }
+
+template <class T> int StepperImpl<T>::stream_function(cudaStream_t st) {
+    NS_TRY(launch(KCOLP, st, false, false, true, false));
+    return launch(KINVP, st, false, false, true, false);
+}
+
+// Enqueue nsteps time steps on `st`.  first_ab1: the first of them is AB1.
+// fft_last: the last step also forms the x-spectrum of its result.
+template <class T>
+int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last) {
+    for (int s = 0; s < nsteps; ++s) {
+        const bool first = first_ab1 && s == 0;
+        NS_TRY(stream_function(st));
+        NS_TRY(launch(KFWDR, st, linear, false, true, first));
+        NS_TRY(launch(KCOLU, st, linear, false, true, first));
+        NS_TRY(launch(KINVR, st, linear, false, true, first));
+        NS_TRY(launch(KFWDP, st, linear, sfd, fft_last || (s + 1 < nsteps), first));
+    }
     return NSSTAB_OK;
 }
 
-template <class T> int StepperImpl<T>::stream_function() {
-    k_col_poisson<T><<<lcolp_.blocks, lcolp_.threads, lcolp_.smem, stream_>>>(f_, lcolp_.per, scale_);
-    NS_LAUNCH_CHECK();
-    k_row_inverse<T><<<linv_pairs_.blocks, linv_pairs_.threads, linv_pairs_.smem, stream_>>>(
-        f_, f_.X2, f_.X2, f_.P, f_.P, linv_pairs_.per, linv_pairs_.logper, true);
-    NS_LAUNCH_CHECK();
-    return NSSTAB_OK;
-}
-
-template <class T> int StepperImpl<T>::run_steps(int nsteps, bool linear, bool sfd, bool fft_last) {
+// Run nsteps steps on the stepper's stream.  Long runs replay CUDA graphs of
+// up to kGraphChunk steps, captured once per (length, flags) on a private
+// stream and launched into the stepper's stream; the AB2 history carries
+// from one chunk to the next through the workspace.
+template <class T> int StepperImpl<T>::run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1) {
     if (linear && !have_base_) {
         set_error("linearised step requested before a base flow was set");
         return NSSTAB_ERR_INVALID_ARG;
     }
-    for (int s = 0; s < nsteps; ++s) {
-        const bool first = (s == 0);
-        NS_TRY(stream_function());
-        if (linear)
-            k_row_forward<T, FWD_RHS_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
-        else
-            k_row_forward<T, FWD_RHS_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
-        NS_LAUNCH_CHECK();
-        const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
-        k_col_update<T><<<lcolu_.blocks, lcolu_.threads, lcolu_.smem, stream_>>>(f_, lcolu_.per, c1, c0, first);
-        NS_LAUNCH_CHECK();
-        k_row_inverse<T><<<linv_rows_.blocks, linv_rows_.threads, linv_rows_.smem, stream_>>>(
-            f_, f_.X1, f_.X2, f_.W, f_.P, linv_rows_.per, linv_rows_.logper, false);
-        NS_LAUNCH_CHECK();
-        const bool do_fft = fft_last || (s + 1 < nsteps);
-        if (linear)
-            k_row_forward<T, FWD_PEN_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, sfd, do_fft);
-        else
-            k_row_forward<T, FWD_PEN_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, sfd, do_fft);
-        NS_LAUNCH_CHECK();
+    if (nsteps < 4) return issue_steps(stream_, nsteps, linear, sfd, first_ab1, fft_last);
+    int done = 0;
+    while (done < nsteps) {
+        const int len = std::min(kGraphChunk, nsteps - done);
+        const bool first = first_ab1 && done == 0;
+        const bool last_fft = (done + len < nsteps) || fft_last;
+        const GraphKey key{len, (linear ? 1 : 0) | (sfd ? 2 : 0) | (first ? 4 : 0) | (last_fft ? 8 : 0)};
+        auto it = graphs_.find(key);
+        if (it == graphs_.end()) {
+            cudaGraph_t g = nullptr;
+            NS_CUDA(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
+            const int rc = issue_steps(cap_, len, linear, sfd, first, last_fft);
+            const cudaError_t ec = cudaStreamEndCapture(cap_, &g);
+            if (rc != NSSTAB_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            NS_CUDA(ec);
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ei = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            NS_CUDA(ei);
+            it = graphs_.emplace(key, ex).first;
+        }
+        NS_CUDA(cudaGraphLaunch(it->second, stream_));
+        done += len;
     }
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::time_kernel(int kid, const Launch& L, int reps, float* ms) {
+    const Launch saved = plan_[kid];
+    plan_[kid] = L;
+    cudaEvent_t e0, e1;
+    NS_CUDA(cudaEventCreate(&e0));
+    NS_CUDA(cudaEventCreate(&e1));
+    int rc = launch(kid, stream_, false, false, true, false);   // warm-up
+    if (rc == NSSTAB_OK) {
+        cudaEventRecord(e0, stream_);
+        for (int r = 0; r < reps && rc == NSSTAB_OK; ++r) rc = launch(kid, stream_, false, false, true, false);
+        cudaEventRecord(e1, stream_);
+        const cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess && rc == NSSTAB_OK) {
+            set_error(std::string("autotune: ") + cudaGetErrorString(e));
+            rc = NSSTAB_ERR_CUDA;
+        }
+        cudaEventElapsedTime(ms, e0, e1);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    plan_[kid] = saved;
+    return rc;
+}
+
+// Measure every valid (elements per thread, sequences per block) pair of
+// each kernel on this grid and keep the fastest.  Clobbers the workspace
+// (never the base flow).  chosen[2k], chosen[2k+1] = (le, per) of kernel k.
+template <class T> int StepperImpl<T>::autotune(int reps, int* chosen) {
+    for (int kid = 0; kid < kNumStepKernels; ++kid) {
+        Launch best = plan_[kid];
+        float best_ms = 1e30f;
+        for (int le = 1; le <= 3; ++le) {
+            for (int per = 1; per <= 16; per *= 2) {
+                const Launch L = make_plan(kid, le, per);
+                if (!L.ok || L.threads < 32 || L.threads > max_threads_for<T>(kid, le)) continue;
+                NS_TRY(set_smem_attr(kid, L));
+                float ms = 0.f;
+                NS_TRY(time_kernel(kid, L, reps, &ms));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = L;
+                }
+            }
+        }
+        NS_TRY(set_plan(kid, best.le, best.per));
+        if (chosen) {
+            chosen[2 * kid] = best.le;
+            chosen[2 * kid + 1] = best.per;
+        }
+    }
+    // restore the shared inverse-row smem attribute for both launches
+    NS_TRY(set_plan(KINVP, plan_[KINVP].le, plan_[KINVP].per));
+    NS_TRY(set_plan(KINVR, plan_[KINVR].le, plan_[KINVR].per));
     return NSSTAB_OK;
 }
 
@@ -676,24 +937,13 @@ template <class T> int StepperImpl<T>::profile_linear(const double* v, int nstep
     if (rc == NSSTAB_OK) rc = transform_W();
     for (int s = 0; s < nsteps && rc == NSSTAB_OK; ++s) {
         const bool first = (s == 0);
-        const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
-        cudaEventRecord(ev[0], stream_);
-        k_col_poisson<T><<<lcolp_.blocks, lcolp_.threads, lcolp_.smem, stream_>>>(f_, lcolp_.per, scale_);
-        cudaEventRecord(ev[1], stream_);
-        k_row_inverse<T><<<linv_pairs_.blocks, linv_pairs_.threads, linv_pairs_.smem, stream_>>>(
-            f_, f_.X2, f_.X2, f_.P, f_.P, linv_pairs_.per, linv_pairs_.logper, true);
-        cudaEventRecord(ev[2], stream_);
-        k_row_forward<T, FWD_RHS_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
-        cudaEventRecord(ev[3], stream_);
-        k_col_update<T><<<lcolu_.blocks, lcolu_.threads, lcolu_.smem, stream_>>>(f_, lcolu_.per, c1, c0, first);
-        cudaEventRecord(ev[4], stream_);
-        k_row_inverse<T><<<linv_rows_.blocks, linv_rows_.threads, linv_rows_.smem, stream_>>>(
-            f_, f_.X1, f_.X2, f_.W, f_.P, linv_rows_.per, linv_rows_.logper, false);
-        cudaEventRecord(ev[5], stream_);
-        k_row_forward<T, FWD_PEN_LIN><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
-        cudaEventRecord(ev[6], stream_);
-        cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaEventSynchronize(ev[6]);
+        for (int k = 0; k < kNumStepKernels && rc == NSSTAB_OK; ++k) {
+            cudaEventRecord(ev[k], stream_);
+            rc = launch(k, stream_, true, false, true, first);
+        }
+        cudaEventRecord(ev[kNumStepKernels], stream_);
+        if (rc != NSSTAB_OK) break;
+        const cudaError_t e = cudaEventSynchronize(ev[kNumStepKernels]);
         if (e != cudaSuccess) {
             set_error(std::string("profile: ") + cudaGetErrorString(e));
             rc = NSSTAB_ERR_CUDA;
@@ -712,7 +962,7 @@ template <class T> int StepperImpl<T>::profile_linear(const double* v, int nstep
 template <class T> int StepperImpl<T>::poisson(const double* omega, double* psi) {
     NS_TRY(load(omega, f_.W));
     NS_TRY(transform_W());
-    NS_TRY(stream_function());
+    NS_TRY(stream_function(stream_));
     return store(f_.P, psi);
 }
 
@@ -733,10 +983,11 @@ template <class T> int StepperImpl<T>::set_base(const double* base_omega) {
         NS_TRY(dalloc(&DxOb, n_));
         NS_TRY(dalloc(&DyOb, n_));
         f_.Ub = Ub; f_.Vb = Vb; f_.DxOb = DxOb; f_.DyOb = DyOb;
+        clear_graphs();   // captured kernels carry the field pointers by value
     }
     NS_TRY(load(base_omega, f_.W));
     NS_TRY(transform_W());
-    NS_TRY(stream_function());   // P = Psi_b
+    NS_TRY(stream_function(stream_));   // P = Psi_b
     k_base_fields<T><<<304, 256, 0, stream_>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb, (T*)f_.DyOb);
     NS_LAUNCH_CHECK();
     have_base_ = true;
@@ -786,8 +1037,10 @@ int StepperImpl<T>::sfd(double* omega, double chi, double Delta, double tol, lon
     }
     if (!Wsave_) NS_TRY(dalloc(&Wsave_, n_));
     if (!Nhsave_) NS_TRY(dalloc(&Nhsave_, (size_t)nxh_ * ny_));
-    f_.sfd_k1 = (T)(cfg_.dt * chi);
-    f_.sfd_k2 = (T)(cfg_.dt / Delta);
+    const T k1 = (T)(cfg_.dt * chi), k2 = (T)(cfg_.dt / Delta);
+    f_.sfd_k1 = k1;
+    f_.sfd_k2 = k2;
+    clear_graphs();   // captured kernels carry the gains and the Y pointer by value
     NS_TRY(load(omega, f_.W));
     NS_CUDA(cudaMemcpyAsync(f_.Y, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
     NS_TRY(transform_W());
@@ -800,20 +1053,7 @@ int StepperImpl<T>::sfd(double* omega, double chi, double Delta, double tol, lon
     while (k < max_steps) {
         const long chunk = std::min<long>(check_every, max_steps - k);
         // the AB2 history continues across chunks: only the very first step is AB1
-        for (long s = 0; s < chunk; ++s) {
-            const bool first = first_chunk && s == 0;
-            NS_TRY(stream_function());
-            k_row_forward<T, FWD_RHS_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, false, true);
-            NS_LAUNCH_CHECK();
-            const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
-            k_col_update<T><<<lcolu_.blocks, lcolu_.threads, lcolu_.smem, stream_>>>(f_, lcolu_.per, c1, c0, first);
-            NS_LAUNCH_CHECK();
-            k_row_inverse<T><<<linv_rows_.blocks, linv_rows_.threads, linv_rows_.smem, stream_>>>(
-                f_, f_.X1, f_.X2, f_.W, f_.P, linv_rows_.per, linv_rows_.logper, false);
-            NS_LAUNCH_CHECK();
-            k_row_forward<T, FWD_PEN_NL><<<lfwd_.blocks, lfwd_.threads, lfwd_.smem, stream_>>>(f_, lfwd_.per, lfwd_.logper, true, true);
-            NS_LAUNCH_CHECK();
-        }
+        NS_TRY(run_steps((int)chunk, false, true, true, first_chunk));
         first_chunk = false;
         k += chunk;
         // residual of the current X with one plain AB1 step, then restore the state

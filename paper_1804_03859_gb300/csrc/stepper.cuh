@@ -21,6 +21,11 @@ struct StepperBase {
     // time each kernel of `nsteps` linearised steps from v with CUDA events
     // on the stepper's stream; ms[k] accumulates kernel k (kNumStepKernels)
     virtual int profile_linear(const double* v, int nsteps, double* ms) = 0;
+    // time every valid launch configuration of each step kernel and keep the
+    // fastest; chosen[2k], chosen[2k+1] = (log2 elements per thread, sequences per block)
+    virtual int autotune(int reps, int* chosen) = 0;
+    virtual int plan_of(int kid, int* le, int* per) const = 0;
+    virtual int set_plan(int kid, int le, int per) = 0;
 };
 
 constexpr int kNumStepKernels = 6;   // col_poisson, row_inverse(psi), row_forward(rhs),

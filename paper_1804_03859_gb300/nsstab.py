@@ -58,6 +58,9 @@ SIGNATURES = [
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                     ctypes.c_void_p, _ip, _ip, _ip]),
     ("stepper_profile_linear", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _dp]),
+    ("stepper_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
+    ("stepper_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("stepper_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, _ip]),
     ("cgs2_orthogonalize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
                                           ctypes.c_void_p, _dp, _dp, ctypes.c_void_p]),
     ("cgs2_orthogonalize_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
@@ -307,6 +310,24 @@ class Stepper:
         _check(self._lib.stepper_profile_linear(self._h, self._p(v, "v"), int(nsteps), ms.ctypes.data_as(_dp)),
                "stepper_profile_linear")
         return dict(zip(self.KERNELS, ms.tolist()))
+
+    def stepper_autotune(self, reps: int = 10) -> dict:
+        """Time every valid launch plan of each kernel and keep the fastest."""
+        plans = (ctypes.c_int * 12)()
+        _check(self._lib.stepper_autotune(self._h, int(reps), plans), "stepper_autotune")
+        return {k: (plans[2 * i], plans[2 * i + 1]) for i, k in enumerate(self.KERNELS)}
+
+    def stepper_set_plan(self, kernel: int, log2_elems: int, per_block: int):
+        _check(self._lib.stepper_set_plan(self._h, int(kernel), int(log2_elems), int(per_block)), "stepper_set_plan")
+
+    def stepper_get_plan(self, kernel: int):
+        le, per = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.stepper_get_plan(self._h, int(kernel), ctypes.byref(le), ctypes.byref(per)),
+               "stepper_get_plan")
+        return le.value, per.value
+
+    def plans(self) -> dict:
+        return {k: self.stepper_get_plan(i) for i, k in enumerate(self.KERNELS)}
 
     def steps_for(self, T: float) -> int:
         k = int(round(T / self.cfg.dt))

@@ -200,3 +200,67 @@ def test_full_size_single_step(nx, ny, prec):
     st.apply_expTL(_dev(w0), _dev(v), out, cfg.dt)
     ref, _ = ns2d.step(v, None, cfg, first=True, base=ns2d.Base.from_omega(w0, cfg))
     assert _rel(_host(out), ref) <= tol
+
+
+def test_every_launch_plan_gives_the_same_step():
+    """Each kernel under every valid (elements per thread, sequences per block)
+    plan reproduces the oracle step: the plans change the radix and the launch
+    shape, never the method."""
+    kw = _cfg(64, 32)
+    cfg = ns2d.Config(**kw)
+    w0 = inputs.wake_like_field(32, 64, seed=21)
+    base = inputs.wake_like_field(32, 64, seed=22)
+    v = inputs.gaussian_field(32, 64, seed=23)
+    ref_nl = ns2d.step_nonlinear(w0, 3, cfg)
+    ref_lin = ns2d.apply_expTL(ns2d.Base.from_omega(base, cfg), v, 3 * cfg.dt, cfg)
+    st = nsstab.Stepper(**kw)
+    defaults = st.plans()
+    tried = 0
+    for kid in range(6):
+        for le in (1, 2, 3):
+            for per in (1, 2, 4, 8):
+                try:
+                    st.stepper_set_plan(kid, le, per)
+                except nsstab.NsstabError:
+                    continue
+                tried += 1
+                t = _dev(w0)
+                st.step_nonlinear(t, 3)
+                assert _rel(_host(t), ref_nl) <= 3e-12, (kid, le, per)
+                out = torch.empty(32, 64, dtype=torch.float64, device="cuda")
+                st.apply_expTL(_dev(base), _dev(v), out, 3 * cfg.dt)
+                assert _rel(_host(out), ref_lin) <= 3e-12, (kid, le, per)
+        st.stepper_set_plan(kid, *defaults[nsstab.Stepper.KERNELS[kid]])
+    assert tried >= 30
+    with pytest.raises(nsstab.NsstabError):
+        st.stepper_set_plan(0, 4, 1)
+
+
+@pytest.mark.parametrize("nx,ny,prec", [(128, 64, 64), (512, 256, 64), (512, 256, 32)])
+def test_autotuned_plans_keep_parity(nx, ny, prec):
+    kw = _cfg(nx, ny)
+    cfg = ns2d.Config(**kw)
+    st = nsstab.Stepper(precision=prec, **kw)
+    chosen = st.stepper_autotune(reps=3)
+    assert set(chosen) == set(nsstab.Stepper.KERNELS)
+    assert st.plans() == chosen
+    w0 = inputs.wake_like_field(ny, nx, seed=24)
+    t = _dev(w0)
+    st.step_nonlinear(t, 2)
+    tol = 2e-12 if prec == 64 else 2 * _tol32(nx, ny)
+    assert _rel(_host(t), ns2d.step_nonlinear(w0, 2, cfg)) <= tol
+
+
+def test_long_runs_through_several_graph_chunks():
+    """300 steps: one captured 256-step chunk plus a 44-step chunk."""
+    kw = _cfg(64, 32, dt=0.02)
+    cfg = ns2d.Config(**kw)
+    st = nsstab.Stepper(**kw)
+    t = torch.zeros(32, 64, dtype=torch.float64, device="cuda")
+    st.step_nonlinear(t, 300)
+    ref = ns2d.step_nonlinear(np.zeros((32, 64)), 300, cfg)
+    assert _rel(_host(t), ref) <= 300 * 1e-12
+    # replaying the cached graphs gives bit-identical results
+    t2 = torch.zeros(32, 64, dtype=torch.float64, device="cuda")
+    st.step_nonlinear(t2, 300)
+    assert torch.equal(t, t2)
