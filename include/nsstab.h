@@ -75,6 +75,25 @@ void nsstab_config_default(nsstab_config* cfg);
  * Errors: INVALID_ARG (bad sizes or parameters), OUT_OF_MEMORY, CUDA. */
 int stepper_create(const nsstab_config* cfg, void* stream, nsstab_stepper** out);
 
+/* Batched stepper: B = nsets * per_set members on one grid, advanced
+ * together by every call below (each kernel launch covers all members).
+ * Member m belongs to parameter set m / per_set, which has its own Reynolds
+ * number Re[k] and cylinder diameter cyl_D[k] (host arrays of nsets; NULL
+ * takes cfg's value for every set) and its own base flow for the linearised
+ * step.  Uses: Reynolds/geometry sweeps (per_set = 1), several start
+ * vectors or perturbations per parameter set (per_set > 1), independent
+ * stability solves served together.  For a batched stepper every field
+ * argument of the calls below is [B][ny][nx] (base flows [nsets][ny][nx]),
+ * stepper_residual and sfd_baseflow write B residuals, and arnoldi_eigs is
+ * replaced by batch_arnoldi_eigs.  A stepper from stepper_create is the
+ * batch nsets = per_set = 1.  Errors: INVALID_ARG (nsets < 1, per_set < 1,
+ * B > 65535, Re <= 0, cyl_D < 0), OUT_OF_MEMORY, CUDA. */
+int batch_create(const nsstab_config* cfg, int nsets, const double* Re, const double* cyl_D,
+                 int per_set, void* stream, nsstab_stepper** out);
+
+/* Number of members B and of parameter sets of a stepper (host ints). */
+int stepper_members(nsstab_stepper* st, int* members, int* sets);
+
 /* Release the stepper and its device memory (synchronises its stream). */
 void stepper_destroy(nsstab_stepper* st);
 
@@ -189,6 +208,22 @@ int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, doub
 int stepper_autotune(nsstab_stepper* st, int reps, int* plans);
 int stepper_set_plan(nsstab_stepper* st, int kernel, int log2_elems, int per_block);
 int stepper_get_plan(nsstab_stepper* st, int kernel, int* log2_elems, int* per_block);
+
+/* arnoldi_eigs for every member of a batched stepper at once: member b runs
+ * its own Arnoldi / Krylov-Schur process (same m, nev, tol, max_restarts, T)
+ * from v0[b] about the base flow of its parameter set.  The processes
+ * advance in lockstep rounds of one batched product with M and one batched
+ * CGS2; a member leaves the batch when it has converged or used its
+ * restarts.  base_omegas: device [nsets][ny][nx] or NULL (current bases);
+ * v0: device [B][ny][nx]; eig_re, eig_im, resid: host [B][nev+1]; eigvecs:
+ * device [B][nev+1][ny][nx] or NULL; n_eig, n_conv, n_matvec: host [B].
+ * Allocates B (n (m+1)) doubles for the bases during the call.  Returns
+ * NSSTAB_OK when every member converged, else NSSTAB_NOT_CONVERGED.
+ * Synchronous. */
+int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const double* v0,
+                       int m, int nev, double tol, int max_restarts, double T,
+                       double* eig_re, double* eig_im, double* resid, double* eigvecs,
+                       int* n_eig, int* n_conv, int* n_matvec);
 
 /* One CGS2 orthogonalisation (Algorithm 1's Gram-Schmidt step applied
  * twice): h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2;

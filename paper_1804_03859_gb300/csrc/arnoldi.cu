@@ -2,11 +2,18 @@
 // Krylov-Schur restart (Sec. 3.2.2, Eqs. 60-63) around the matrix-free
 // propagator M v = exp(T A) v of the stepper.
 //
-// Device / host split: every length-n vector (the basis V, the products
-// M v, the Gram-Schmidt updates) stays on the GPU; only the j+1 projection
-// coefficients and beta of each step come back (one small D2H copy per
-// Krylov step), and the m x m projected matrix is factorised on the host in
-// FP64 (dense_eig.cpp).
+// The driver runs the independent eigenproblems of every member of a batched
+// stepper in lockstep rounds: each round is one batched product with M (one
+// set of step kernels for all members still working), one batched CGS2 and,
+// per member, the update of its projected matrix; a member whose
+// factorisation is full is checked for convergence and either finishes or is
+// restarted, and finished members leave the batch (their blocks return at
+// once).  A single stepper is the batch of one.
+//
+// Device / host split: every length-n vector (the bases, the products, the
+// Gram-Schmidt updates) stays on the GPU; per round only the coefficients
+// and beta of each member come back (one small D2H copy), and the m x m
+// projected matrices are factorised on the host in FP64 (dense_eig.cpp).
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -51,8 +58,6 @@ int take_leading(const std::vector<dense::cd>& ev, const std::vector<int>& order
 
 // eigenvector (unit norm, length mm) of the Schur form for eigenvalue index i
 std::vector<dense::cd> ritz_vector(int mm, const double* Tm, const double* Zm, const std::vector<dense::cd>& ev, int i) {
-    // block start of eigenvalue i: a 2x2 block starts at i if T(i+1,i) != 0,
-    // or at i-1 if T(i,i-1) != 0
     if (i > 0 && Tm[i + (size_t)(i - 1) * mm] != 0.0) {
         std::vector<dense::cd> y = dense::schur_eigenvector(mm, Tm, Zm, i - 1, ev[i - 1]);
         for (auto& v : y) v = std::conj(v);
@@ -61,161 +66,234 @@ std::vector<dense::cd> ritz_vector(int mm, const double* Tm, const double* Zm, c
     return dense::schur_eigenvector(mm, Tm, Zm, i, ev[i]);
 }
 
-}  // namespace
-
-int arnoldi_run(StepperBase* st, GsWork& gs, cudaStream_t stream, const nsstab_config& cfg, long n,
-                const double* v0, int m, int nev, double tol, int max_restarts, int nsteps, ArnoldiOut& out) {
-    const double delta = 0.05;   // wanted set |mu| >= 1 - delta (Sec. 3.2.2)
-    DevBuf V, tmp, Cd;
-    NS_CUDA(cudaMalloc(&V.p, (size_t)n * (m + 1) * sizeof(double)));
-    NS_CUDA(cudaMalloc(&Cd.p, (size_t)(m + 1) * (m + 1) * sizeof(double)));
-    NS_TRY(gs.alloc(m + 1));
-    double nrm = 0.0;
-    NS_TRY(vec_norm(v0, n, &nrm, gs, stream));
-    if (!(nrm > 0.0) || !std::isfinite(nrm)) {
-        set_error("arnoldi_eigs: starting vector has zero or non-finite norm");
-        return NSSTAB_ERR_INVALID_ARG;
-    }
-    NS_TRY(vec_scale(V.p, v0, n, 1.0 / nrm, stream));
-    const int ldb = m + 1;
-    std::vector<double> B((size_t)ldb * m, 0.0), h(m + 1);
-    auto Bat = [&](int i, int j) -> double& { return B[i + (size_t)j * ldb]; };
-    int j0 = 0, restarts = 0, matvec = 0;
-    bool hessenberg_form = true;
-    std::vector<double> Tm, Zm;
+// Per-member state of the Krylov process.
+struct Member {
+    double* V = nullptr;            // device basis, n x (m+1)
+    std::vector<double> B;          // projected matrix, (m+1) x m column-major
+    int j = 0;                      // columns filled
+    int restarts = 0, matvec = 0;
+    bool hessenberg = true;         // B is upper Hessenberg (no restart yet)
+    bool done = false, breakdown = false;
+    int mm = 0;                     // order of the last factorisation
+    double betam = 0.0;
+    std::vector<double> Tm, Zm;     // Schur form of B_mm
     std::vector<dense::cd> ev;
     std::vector<int> order;
-    int k = 0, mm = m;
-    double betam = 0.0;
-    bool breakdown = false;
     std::vector<double> res;
+    int k = 0, conv = 0;
+};
+
+}  // namespace
+
+int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* v0, int m, int nev, double tol,
+                      int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs) {
+    const double delta = 0.05;   // wanted set |mu| >= 1 - delta (Sec. 3.2.2)
+    const int nb = st->members();
+    outs.resize(nb);
+    const int ldb = m + 1;
+    DevBuf Vall, tmp, Cd;
+    NS_CUDA(cudaMalloc(&Vall.p, (size_t)nb * n * (m + 1) * sizeof(double)));
+    NS_CUDA(cudaMalloc(&Cd.p, (size_t)(m + 1) * (m + 1) * sizeof(double)));
+    GsBatch gs;
+    struct Release {
+        GsBatch& g;
+        ~Release() { g.release(); }
+    } rel{gs};
+    NS_TRY(gs.alloc(nb, m + 1));
+    std::vector<Member> mem(nb);
+    // v_1 = v0 / ||v0|| for every member
+    {
+        std::vector<const double*> V0(nb);
+        std::vector<double*> W0(nb);
+        std::vector<int> j0(nb, 0);
+        std::vector<double> h(1), beta(nb), inv(nb);
+        for (int b = 0; b < nb; ++b) {
+            mem[b].V = Vall.p + (size_t)b * n * (m + 1);
+            mem[b].B.assign((size_t)ldb * m, 0.0);
+            NS_CUDA(cudaMemcpyAsync(mem[b].V, v0 + (size_t)b * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    stream));
+            V0[b] = mem[b].V;
+            W0[b] = mem[b].V;
+        }
+        NS_TRY(cgs2_batch(nb, V0.data(), n, n, j0.data(), W0.data(), h.data(), 0, beta.data(), gs, stream));
+        for (int b = 0; b < nb; ++b) {
+            if (!(beta[b] > 0.0) || !std::isfinite(beta[b])) {
+                set_error("arnoldi_eigs: starting vector has zero or non-finite norm");
+                return NSSTAB_ERR_INVALID_ARG;
+            }
+            inv[b] = 1.0 / beta[b];
+        }
+        NS_TRY(scale_batch(nb, W0.data(), n, inv.data(), gs, stream));
+    }
+    std::vector<const double*> in(nb);
+    std::vector<double*> out(nb), wv(nb);
+    std::vector<const double*> Vp(nb);
+    std::vector<int> jv(nb);
+    std::vector<double> H((size_t)nb * (m + 1)), beta(nb), inv(nb);
     while (true) {
-        mm = m;
-        breakdown = false;
-        for (int j = j0; j < m; ++j) {
-            double* vj = V.p + (size_t)j * n;
-            double* w = V.p + (size_t)(j + 1) * n;
-            NS_TRY(st->step_linear(vj, w, nsteps));
-            ++matvec;
-            double beta = 0.0;
-            NS_TRY(cgs2(V.p, n, n, j + 1, w, h.data(), &beta, gs, stream));
+        int active = 0;
+        for (int b = 0; b < nb; ++b) {
+            Member& M = mem[b];
+            if (M.done) {
+                in[b] = nullptr;
+                out[b] = nullptr;
+                jv[b] = -1;
+                wv[b] = nullptr;
+                Vp[b] = M.V;
+                continue;
+            }
+            ++active;
+            in[b] = M.V + (size_t)M.j * n;
+            out[b] = M.V + (size_t)(M.j + 1) * n;
+            wv[b] = out[b];
+            Vp[b] = M.V;
+            jv[b] = M.j + 1;
+        }
+        if (active == 0) break;
+        // one batched product with M, one batched CGS2
+        NS_TRY(st->step_linear_ptrs(in.data(), out.data(), nsteps));
+        NS_TRY(cgs2_batch(nb, Vp.data(), n, n, jv.data(), wv.data(), H.data(), m + 1, beta.data(), gs, stream));
+        std::fill(inv.begin(), inv.end(), 0.0);
+        std::vector<double*> scale_ptr(nb, nullptr);
+        for (int b = 0; b < nb; ++b) {
+            Member& M = mem[b];
+            if (M.done) continue;
+            const int j = M.j;
+            ++M.matvec;
             double hn = 0.0;
             for (int i = 0; i <= j; ++i) {
-                Bat(i, j) = h[i];
-                hn += h[i] * h[i];
+                M.B[i + (size_t)j * ldb] = H[(size_t)b * (m + 1) + i];
+                hn += H[(size_t)b * (m + 1) + i] * H[(size_t)b * (m + 1) + i];
             }
-            Bat(j + 1, j) = beta;
-            if (!std::isfinite(beta)) {
+            M.B[(j + 1) + (size_t)j * ldb] = beta[b];
+            if (!std::isfinite(beta[b])) {
                 set_error("arnoldi_eigs: non-finite values in the Krylov basis");
-                out.status = NSSTAB_DIVERGED;
                 return NSSTAB_DIVERGED;
             }
-            if (beta <= 1e-14 * std::max(1.0, std::sqrt(hn))) {   // invariant subspace
-                mm = j + 1;
-                breakdown = true;
-                break;
-            }
-            NS_TRY(vec_scale(w, w, n, 1.0 / beta, stream));
-        }
-        betam = breakdown ? 0.0 : Bat(mm, mm - 1);
-        // Schur form of the projected matrix B_mm
-        Tm.assign((size_t)mm * mm, 0.0);
-        Zm.assign((size_t)mm * mm, 0.0);
-        for (int j = 0; j < mm; ++j) {
-            Zm[j + (size_t)j * mm] = 1.0;
-            for (int i = 0; i < mm; ++i) Tm[i + (size_t)j * mm] = Bat(i, j);
-        }
-        if (!hessenberg_form) dense::hessenberg(mm, Tm.data(), Zm.data());
-        if (dense::schur(mm, Tm.data(), Zm.data()) != 0) {
-            set_error("arnoldi_eigs: QR iteration on the projected matrix did not converge");
-            return NSSTAB_ERR_NUMERICAL;
-        }
-        ev = dense::schur_eigenvalues(mm, Tm.data());
-        order = leading_order(ev);
-        k = take_leading(ev, order, nev);
-        res.assign(k, 0.0);
-        int conv = 0;
-        for (int s = 0; s < k; ++s) {
-            const std::vector<dense::cd> y = ritz_vector(mm, Tm.data(), Zm.data(), ev, order[s]);
-            res[s] = std::abs(betam * y[mm - 1]);   // Eq. 63
-            if (res[s] <= tol) ++conv;
-        }
-        out.n_conv = conv;
-        if (conv >= k || restarts >= max_restarts || breakdown) break;
-        // ---- Krylov-Schur restart: keep the p wanted Ritz values
-        int p = 0;
-        for (const auto& e : ev)
-            if (std::abs(e) >= 1.0 - delta) ++p;
-        p = std::max(k, std::min(p, mm / 2));
-        {
-            const dense::cd thr_mu = ev[order[p - 1]];
-            if (thr_mu.imag() != 0.0 && p < mm) {
-                for (int s = p; s < mm; ++s)
-                    if (std::abs(ev[order[s]] - std::conj(thr_mu)) <= 1e-12 * std::max(1.0, std::abs(thr_mu))) {
-                        ++p;
-                        break;
-                    }
+            M.j = j + 1;
+            if (beta[b] <= 1e-14 * std::max(1.0, std::sqrt(hn))) {   // invariant subspace
+                M.breakdown = true;
+            } else {
+                inv[b] = 1.0 / beta[b];
+                scale_ptr[b] = out[b];
             }
         }
-        std::vector<double> mags(mm);
-        for (int s = 0; s < mm; ++s) mags[s] = std::abs(ev[s]);
-        std::sort(mags.begin(), mags.end(), std::greater<double>());
-        const double thr = mags[p - 1] * (1.0 - 1e-12);
-        const int psel = dense::schur_reorder(mm, Tm.data(), Zm.data(), [&](dense::cd e) { return std::abs(e) >= thr; });
-        if (psel <= 0 || psel >= mm) {
-            set_error("arnoldi_eigs: Schur reordering failed");
-            return NSSTAB_ERR_NUMERICAL;
+        NS_TRY(scale_batch(nb, scale_ptr.data(), n, inv.data(), gs, stream));
+        // members with a full factorisation: Ritz pairs, convergence, restart
+        for (int b = 0; b < nb; ++b) {
+            Member& M = mem[b];
+            if (M.done || (M.j < m && !M.breakdown)) continue;
+            const int mm = M.j;
+            M.mm = mm;
+            M.betam = M.breakdown ? 0.0 : M.B[mm + (size_t)(mm - 1) * ldb];
+            M.Tm.assign((size_t)mm * mm, 0.0);
+            M.Zm.assign((size_t)mm * mm, 0.0);
+            for (int jj = 0; jj < mm; ++jj) {
+                M.Zm[jj + (size_t)jj * mm] = 1.0;
+                for (int i = 0; i < mm; ++i) M.Tm[i + (size_t)jj * mm] = M.B[i + (size_t)jj * ldb];
+            }
+            if (!M.hessenberg) dense::hessenberg(mm, M.Tm.data(), M.Zm.data());
+            if (dense::schur(mm, M.Tm.data(), M.Zm.data()) != 0) {
+                set_error("arnoldi_eigs: QR iteration on the projected matrix did not converge");
+                return NSSTAB_ERR_NUMERICAL;
+            }
+            M.ev = dense::schur_eigenvalues(mm, M.Tm.data());
+            M.order = leading_order(M.ev);
+            M.k = take_leading(M.ev, M.order, nev);
+            M.res.assign(M.k, 0.0);
+            M.conv = 0;
+            for (int s = 0; s < M.k; ++s) {
+                const std::vector<dense::cd> y = ritz_vector(mm, M.Tm.data(), M.Zm.data(), M.ev, M.order[s]);
+                M.res[s] = std::abs(M.betam * y[mm - 1]);   // Eq. 63
+                if (M.res[s] <= tol) ++M.conv;
+            }
+            if (M.conv >= M.k || M.restarts >= max_restarts || M.breakdown) {
+                M.done = true;
+                continue;
+            }
+            // ---- Krylov-Schur restart: keep the p wanted Ritz values
+            int p = 0;
+            for (const auto& e : M.ev)
+                if (std::abs(e) >= 1.0 - delta) ++p;
+            p = std::max(M.k, std::min(p, mm / 2));
+            {
+                const dense::cd thr_mu = M.ev[M.order[p - 1]];
+                if (thr_mu.imag() != 0.0 && p < mm) {
+                    for (int s = p; s < mm; ++s)
+                        if (std::abs(M.ev[M.order[s]] - std::conj(thr_mu)) <= 1e-12 * std::max(1.0, std::abs(thr_mu))) {
+                            ++p;
+                            break;
+                        }
+                }
+            }
+            std::vector<double> mags(mm);
+            for (int s = 0; s < mm; ++s) mags[s] = std::abs(M.ev[s]);
+            std::sort(mags.begin(), mags.end(), std::greater<double>());
+            const double thr = mags[p - 1] * (1.0 - 1e-12);
+            const int psel =
+                dense::schur_reorder(mm, M.Tm.data(), M.Zm.data(), [&](dense::cd e) { return std::abs(e) >= thr; });
+            if (psel <= 0 || psel >= mm) {
+                set_error("arnoldi_eigs: Schur reordering failed");
+                return NSSTAB_ERR_NUMERICAL;
+            }
+            p = psel;
+            // V_p <- V_mm Z(:, :p), v_{p+1} <- v_{mm+1}
+            if (!tmp.p) NS_CUDA(cudaMalloc(&tmp.p, (size_t)n * m * sizeof(double)));
+            NS_CUDA(cudaMemcpyAsync(Cd.p, M.Zm.data(), (size_t)mm * p * sizeof(double), cudaMemcpyHostToDevice,
+                                    stream));
+            NS_TRY(basis_combine(M.V, n, n, mm, Cd.p, p, tmp.p, n, stream));
+            NS_CUDA(cudaMemcpyAsync(M.V, tmp.p, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+            NS_CUDA(cudaMemcpyAsync(M.V + (size_t)p * n, M.V + (size_t)mm * n, (size_t)n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, stream));
+            // B <- [[S11], [b^T Z(:, :p)]] with b = beta_m e_m
+            std::fill(M.B.begin(), M.B.end(), 0.0);
+            for (int jj = 0; jj < p; ++jj) {
+                for (int i = 0; i < p; ++i) M.B[i + (size_t)jj * ldb] = M.Tm[i + (size_t)jj * mm];
+                M.B[p + (size_t)jj * ldb] = M.betam * M.Zm[(mm - 1) + (size_t)jj * mm];
+            }
+            NS_CUDA(cudaStreamSynchronize(stream));   // Zm upload done before Cd is reused
+            M.j = p;
+            M.hessenberg = false;
+            ++M.restarts;
         }
-        p = psel;
-        // V_p <- V_mm Z(:, :p), v_{p+1} <- v_{mm+1}
-        if (!tmp.p) NS_CUDA(cudaMalloc(&tmp.p, (size_t)n * m * sizeof(double)));
-        NS_CUDA(cudaMemcpyAsync(Cd.p, Zm.data(), (size_t)mm * p * sizeof(double), cudaMemcpyHostToDevice, stream));
-        NS_TRY(basis_combine(V.p, n, n, mm, Cd.p, p, tmp.p, n, stream));
-        NS_CUDA(cudaMemcpyAsync(V.p, tmp.p, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-        NS_CUDA(cudaMemcpyAsync(V.p + (size_t)p * n, V.p + (size_t)mm * n, (size_t)n * sizeof(double),
-                                cudaMemcpyDeviceToDevice, stream));
-        // B <- [[S11], [b^T Z(:, :p)]] with b = beta_m e_m
-        std::fill(B.begin(), B.end(), 0.0);
-        for (int j = 0; j < p; ++j) {
-            for (int i = 0; i < p; ++i) Bat(i, j) = Tm[i + (size_t)j * mm];
-            Bat(p, j) = betam * Zm[(mm - 1) + (size_t)j * mm];
-        }
-        NS_CUDA(cudaStreamSynchronize(stream));   // Zm upload done before reuse
-        j0 = p;
-        hessenberg_form = false;
-        ++restarts;
     }
     // outputs in leading order
-    out.n_eig = k;
-    out.n_matvec = matvec;
-    out.restarts = restarts;
-    out.mu.resize(k);
-    out.resid = res;
-    for (int s = 0; s < k; ++s) out.mu[s] = ev[order[s]];
-    if (out.eigvecs) {
-        // columns of Y (mm x k): real vector, or Re / Im of a conjugate pair
-        std::vector<double> Y((size_t)mm * k, 0.0);
-        int s = 0;
-        while (s < k) {
-            const std::vector<dense::cd> y = ritz_vector(mm, Tm.data(), Zm.data(), ev, order[s]);
-            if (ev[order[s]].imag() != 0.0 && s + 1 < k) {
-                for (int i = 0; i < mm; ++i) {
-                    Y[i + (size_t)s * mm] = y[i].real();
-                    Y[i + (size_t)(s + 1) * mm] = y[i].imag();
+    for (int b = 0; b < nb; ++b) {
+        Member& M = mem[b];
+        ArnoldiOut& o = outs[b];
+        o.n_eig = M.k;
+        o.n_conv = M.conv;
+        o.n_matvec = M.matvec;
+        o.restarts = M.restarts;
+        o.mu.resize(M.k);
+        o.resid = M.res;
+        for (int s = 0; s < M.k; ++s) o.mu[s] = M.ev[M.order[s]];
+        o.status = (o.n_conv >= o.n_eig) ? NSSTAB_OK : NSSTAB_NOT_CONVERGED;
+        if (o.eigvecs) {
+            const int mm = M.mm;
+            // columns of Y (mm x k): real vector, or Re / Im of a conjugate pair
+            std::vector<double> Y((size_t)mm * M.k, 0.0);
+            int s = 0;
+            while (s < M.k) {
+                const std::vector<dense::cd> y = ritz_vector(mm, M.Tm.data(), M.Zm.data(), M.ev, M.order[s]);
+                if (M.ev[M.order[s]].imag() != 0.0 && s + 1 < M.k) {
+                    for (int i = 0; i < mm; ++i) {
+                        Y[i + (size_t)s * mm] = y[i].real();
+                        Y[i + (size_t)(s + 1) * mm] = y[i].imag();
+                    }
+                    s += 2;
+                } else {
+                    for (int i = 0; i < mm; ++i) Y[i + (size_t)s * mm] = y[i].real();
+                    s += 1;
                 }
-                s += 2;
-            } else {
-                for (int i = 0; i < mm; ++i) Y[i + (size_t)s * mm] = y[i].real();
-                s += 1;
             }
+            NS_CUDA(cudaMemcpyAsync(Cd.p, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
+            NS_TRY(basis_combine(M.V, n, n, mm, Cd.p, M.k, o.eigvecs, n, stream));
+            NS_CUDA(cudaStreamSynchronize(stream));
         }
-        NS_CUDA(cudaMemcpyAsync(Cd.p, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
-        NS_TRY(basis_combine(V.p, n, n, mm, Cd.p, k, out.eigvecs, n, stream));
     }
     NS_CUDA(cudaStreamSynchronize(stream));
-    out.status = (out.n_conv >= k) ? NSSTAB_OK : NSSTAB_NOT_CONVERGED;
-    (void)cfg;
-    return out.status;
+    return NSSTAB_OK;
 }
 
 }  // namespace nsstab

@@ -16,8 +16,11 @@ struct ArnoldiOut {
     int status = NSSTAB_OK;
 };
 
-// v0: device n-vector; nsteps = T/dt linearised steps per product with M.
-int arnoldi_run(StepperBase* st, GsWork& gs, cudaStream_t stream, const nsstab_config& cfg, long n,
-                const double* v0, int m, int nev, double tol, int max_restarts, int nsteps, ArnoldiOut& out);
+// One eigenproblem per member of the stepper's batch.  v0: device
+// [members][n]; nsteps = T/dt linearised steps per product with M; outs[b]
+// receives member b's results (set outs[b].eigvecs before the call to get
+// Ritz vectors).
+int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* v0, int m, int nev, double tol,
+                      int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs);
 
 }  // namespace nsstab

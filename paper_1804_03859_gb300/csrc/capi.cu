@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "arnoldi.h"
 #include "dense_eig.h"
@@ -67,9 +68,8 @@ void nsstab_config_default(nsstab_config* c) {
 
 const char* nsstab_last_error(void) { return last_error(); }
 
-int stepper_create(const nsstab_config* cfg, void* stream, nsstab_stepper** out) {
-    if (!cfg || !out) return bad_arg("stepper_create: null argument");
-    *out = nullptr;
+static int create_impl(const nsstab_config* cfg, int nsets, const double* Re, const double* D, int per_set,
+                       void* stream, nsstab_stepper** out) {
     NS_TRY(validate_config(*cfg));
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -81,7 +81,7 @@ int stepper_create(const nsstab_config* cfg, void* stream, nsstab_stepper** out)
     st->cfg = *cfg;
     st->stream = (cudaStream_t)stream;
     st->have_base = false;
-    st->impl = make_stepper(*cfg, st->stream);
+    st->impl = make_stepper(*cfg, nsets, Re, D, per_set, st->stream);
     const int rc = st->impl->init();
     if (rc != NSSTAB_OK) {
         delete st->impl;
@@ -89,6 +89,32 @@ int stepper_create(const nsstab_config* cfg, void* stream, nsstab_stepper** out)
         return rc;
     }
     *out = st;
+    return NSSTAB_OK;
+}
+
+int stepper_create(const nsstab_config* cfg, void* stream, nsstab_stepper** out) {
+    if (!cfg || !out) return bad_arg("stepper_create: null argument");
+    *out = nullptr;
+    return create_impl(cfg, 1, nullptr, nullptr, 1, stream, out);
+}
+
+int batch_create(const nsstab_config* cfg, int nsets, const double* Re, const double* cyl_D, int per_set,
+                 void* stream, nsstab_stepper** out) {
+    if (!cfg || !out) return bad_arg("batch_create: null argument");
+    *out = nullptr;
+    if (nsets < 1 || per_set < 1 || (long)nsets * per_set > 65535)
+        return bad_arg("batch_create: need nsets >= 1, per_set >= 1, nsets * per_set <= 65535");
+    for (int k = 0; k < nsets; ++k) {
+        if (Re && !(Re[k] > 0)) return bad_arg("batch_create: every Re must be positive");
+        if (cyl_D && !(cyl_D[k] >= 0)) return bad_arg("batch_create: every cyl_D must be >= 0");
+    }
+    return create_impl(cfg, nsets, Re, cyl_D, per_set, stream, out);
+}
+
+int stepper_members(nsstab_stepper* st, int* members, int* sets) {
+    if (!st || !members || !sets) return bad_arg("stepper_members: null argument");
+    *members = st->impl->members();
+    *sets = st->impl->sets();
     return NSSTAB_OK;
 }
 
@@ -134,7 +160,9 @@ int apply_expTL(nsstab_stepper* st, const double* base_omega, const double* v_in
 int stepper_residual(nsstab_stepper* st, const double* q, double* r) {
     if (!st || !q || !r) return bad_arg("stepper_residual: null argument");
     NS_TRY(st->impl->residual(q, r));
-    return std::isfinite(*r) ? NSSTAB_OK : NSSTAB_DIVERGED;
+    for (int m = 0; m < st->impl->members(); ++m)
+        if (!std::isfinite(r[m])) return NSSTAB_DIVERGED;
+    return NSSTAB_OK;
 }
 
 int sfd_baseflow(nsstab_stepper* st, double* omega, double chi, double Delta, double tol, long max_steps,
@@ -150,6 +178,7 @@ int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
                  int* n_eig, int* n_conv, int* n_matvec) {
     if (!st || !v0 || !eig_re || !eig_im || !resid || !n_eig || !n_conv || !n_matvec)
         return bad_arg("arnoldi_eigs: null argument");
+    if (st->impl->members() != 1) return bad_arg("arnoldi_eigs: single steppers only (use batch_arnoldi_eigs)");
     const long n = (long)st->cfg.nx * st->cfg.ny;
     if (m < 2 || m > 1024 || m >= n) return bad_arg("arnoldi_eigs: need 2 <= m <= min(nx*ny - 1, 1024)");
     if (nev < 1 || nev >= m) return bad_arg("arnoldi_eigs: need 1 <= nev < m");
@@ -163,10 +192,11 @@ int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
     } else if (!st->have_base) {
         return bad_arg("arnoldi_eigs: no base flow (pass base_omega or call stepper_set_base)");
     }
-    ArnoldiOut out;
-    out.eigvecs = eigvecs;
-    const int rc = arnoldi_run(st->impl, st->gs, st->stream, st->cfg, n, v0, m, nev, tol, max_restarts, nsteps, out);
+    std::vector<ArnoldiOut> outs(1);
+    outs[0].eigvecs = eigvecs;
+    const int rc = arnoldi_batch_run(st->impl, st->stream, n, v0, m, nev, tol, max_restarts, nsteps, outs);
     if (rc < 0) return rc;
+    const ArnoldiOut& out = outs[0];
     for (int s = 0; s < out.n_eig; ++s) {
         eig_re[s] = out.mu[s].real();
         eig_im[s] = out.mu[s].imag();
@@ -175,7 +205,47 @@ int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
     *n_eig = out.n_eig;
     *n_conv = out.n_conv;
     *n_matvec = out.n_matvec;
-    return rc;
+    return rc != NSSTAB_OK ? rc : out.status;
+}
+
+int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const double* v0, int m, int nev, double tol,
+                       int max_restarts, double T, double* eig_re, double* eig_im, double* resid, double* eigvecs,
+                       int* n_eig, int* n_conv, int* n_matvec) {
+    if (!st || !v0 || !eig_re || !eig_im || !resid || !n_eig || !n_conv || !n_matvec)
+        return bad_arg("batch_arnoldi_eigs: null argument");
+    const long n = (long)st->cfg.nx * st->cfg.ny;
+    if (m < 2 || m > 1024 || m >= n) return bad_arg("batch_arnoldi_eigs: need 2 <= m <= min(nx*ny - 1, 1024)");
+    if (nev < 1 || nev >= m) return bad_arg("batch_arnoldi_eigs: need 1 <= nev < m");
+    if (max_restarts < 0) return bad_arg("batch_arnoldi_eigs: max_restarts < 0");
+    if (!(tol >= 0)) return bad_arg("batch_arnoldi_eigs: tol < 0");
+    int nsteps = 0;
+    NS_TRY(steps_for(st->cfg, T, &nsteps));
+    if (base_omegas) {
+        NS_TRY(st->impl->set_base(base_omegas));
+        st->have_base = true;
+    } else if (!st->have_base) {
+        return bad_arg("batch_arnoldi_eigs: no base flows (pass base_omegas or call stepper_set_base)");
+    }
+    const int B = st->impl->members();
+    std::vector<ArnoldiOut> outs(B);
+    if (eigvecs)
+        for (int b = 0; b < B; ++b) outs[b].eigvecs = eigvecs + (size_t)b * (nev + 1) * n;
+    const int rc = arnoldi_batch_run(st->impl, st->stream, n, v0, m, nev, tol, max_restarts, nsteps, outs);
+    if (rc < 0) return rc;
+    int status = rc;
+    for (int b = 0; b < B; ++b) {
+        const ArnoldiOut& o = outs[b];
+        for (int s = 0; s < o.n_eig; ++s) {
+            eig_re[(size_t)b * (nev + 1) + s] = o.mu[s].real();
+            eig_im[(size_t)b * (nev + 1) + s] = o.mu[s].imag();
+            resid[(size_t)b * (nev + 1) + s] = o.resid[s];
+        }
+        n_eig[b] = o.n_eig;
+        n_conv[b] = o.n_conv;
+        n_matvec[b] = o.n_matvec;
+        if (status == NSSTAB_OK && o.status != NSSTAB_OK) status = o.status;
+    }
+    return status;
 }
 
 int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, double* kernel_ms) {

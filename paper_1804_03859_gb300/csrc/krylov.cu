@@ -99,6 +99,178 @@ __global__ void k_combine(const double* __restrict__ V, long ldv, long n, int m,
     }
 }
 
+// ----------------------------------------------------- batched variants
+// Member b (blockIdx.y) works on its own basis V[b] (column-major, leading
+// dimension ldv), vector w[b] and column count j[b]; j[b] <= 0 leaves w[b]
+// alone in the products (the norm pass uses its own count array).
+
+__global__ void k_gs_dot_b(const double* const* __restrict__ Vs, long ldv, long n, const int* __restrict__ js,
+                           const double* const* __restrict__ ws, double* __restrict__ partial, int ldp) {
+    const int b = blockIdx.y;
+    const int j = js[b];
+    if (j <= 0) return;
+    const double* V = Vs[b];
+    const double* w = ws[b];
+    double* part = partial + (size_t)b * gridDim.x * ldp;
+    const long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long r0 = (long)blockIdx.x * chunk;
+    const long r1 = min(n, r0 + chunk);
+    __shared__ double red[kColGroup][kGsThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c0 = 0; c0 < j; c0 += kColGroup) {
+        const int nc = min(kColGroup, j - c0);
+        double acc[kColGroup];
+#pragma unroll
+        for (int cc = 0; cc < kColGroup; ++cc) acc[cc] = 0.0;
+        for (long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const double wi = w[i];
+#pragma unroll
+            for (int cc = 0; cc < kColGroup; ++cc)
+                if (cc < nc) acc[cc] = fma(V[(long)(c0 + cc) * ldv + i], wi, acc[cc]);
+        }
+#pragma unroll
+        for (int cc = 0; cc < kColGroup; ++cc) {
+            double a = acc[cc];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[cc][warp] = a;
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            double s = 0.0;
+            for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) s += red[threadIdx.x][wv];
+            part[(long)blockIdx.x * ldp + c0 + threadIdx.x] = s;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_gs_reduce_b(const double* __restrict__ partial, int nb, int ldp, const int* __restrict__ js,
+                              double* __restrict__ out) {
+    const int b = blockIdx.y;
+    const int j = js[b];
+    const double* part = partial + (size_t)b * nb * ldp;
+    for (int c = threadIdx.x; c < j; c += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < nb; ++k) s += part[(long)k * ldp + c];
+        out[(size_t)b * ldp + c] = s;
+    }
+}
+
+__global__ void k_gs_update_b(double* const* __restrict__ ws, const double* const* __restrict__ Vs, long ldv, long n,
+                              const int* __restrict__ js, const double* __restrict__ h, int ldp) {
+    const int b = blockIdx.y;
+    const int j = js[b];
+    if (j <= 0) return;
+    extern __shared__ double hs[];
+    for (int c = threadIdx.x; c < j; c += blockDim.x) hs[c] = h[(size_t)b * ldp + c];
+    __syncthreads();
+    double* w = ws[b];
+    const double* V = Vs[b];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int c = 0; c < j; ++c) acc = fma(V[(long)c * ldv + i], hs[c], acc);
+        w[i] -= acc;
+    }
+}
+
+__global__ void k_scale_b(double* const* __restrict__ ws, long n, const double* __restrict__ s) {
+    double* w = ws[blockIdx.y];
+    if (!w) return;
+    const double f = s[blockIdx.y];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) w[i] *= f;
+}
+
+int GsBatch::alloc(int nmem, int cols) {
+    if (nmem <= B && cols <= max_cols) return NSSTAB_OK;
+    release();
+    B = nmem;
+    max_cols = cols;
+    grid = 152;
+    const size_t ph = (size_t)B * 3 * max_cols;
+    NS_CUDA(cudaMalloc(&partial, (size_t)B * grid * max_cols * sizeof(double)));
+    NS_CUDA(cudaMalloc(&hdev, ph * sizeof(double)));
+    NS_CUDA(cudaMalloc(&jdev, (size_t)B * 2 * sizeof(int)));
+    NS_CUDA(cudaMalloc(&ptrs, (size_t)B * 2 * sizeof(double*)));
+    NS_CUDA(cudaMalloc(&sdev, (size_t)B * sizeof(double)));
+    NS_CUDA(cudaMallocHost(&hhost, ph * sizeof(double)));
+    return NSSTAB_OK;
+}
+
+void GsBatch::release() {
+    if (partial) cudaFree(partial);
+    if (hdev) cudaFree(hdev);
+    if (jdev) cudaFree(jdev);
+    if (ptrs) cudaFree(ptrs);
+    if (sdev) cudaFree(sdev);
+    if (hhost) cudaFreeHost(hhost);
+    partial = hdev = sdev = hhost = nullptr;
+    jdev = nullptr;
+    ptrs = nullptr;
+    B = max_cols = 0;
+}
+
+// CGS2 of w[b] against the first j[b] columns of V[b] for every member with
+// j[b] >= 0 (j[b] = 0: norm only; j[b] < 0: member skipped); h[b][0..j[b])
+// and beta[b] = ||w[b]|| to the host.  One synchronisation.
+int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j, double* const* w,
+               double* h /*host [nmem][ldh]*/, int ldh, double* beta, GsBatch& ws, cudaStream_t stream) {
+    int jmax = 1;
+    for (int b = 0; b < nmem; ++b) jmax = std::max(jmax, j[b]);
+    NS_TRY(ws.alloc(nmem, jmax));
+    const int ldp = ws.max_cols;
+    std::vector<int> jh(2 * (size_t)nmem);
+    std::vector<const double*> ph(2 * (size_t)nmem);
+    for (int b = 0; b < nmem; ++b) {
+        jh[b] = j[b];
+        jh[nmem + b] = j[b] >= 0 ? 1 : 0;   // j < 0: member inactive in this call
+        ph[b] = V[b];
+        ph[nmem + b] = w[b];
+    }
+    NS_CUDA(cudaMemcpyAsync(ws.jdev, jh.data(), jh.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+    NS_CUDA(cudaMemcpyAsync(ws.ptrs, ph.data(), ph.size() * sizeof(double*), cudaMemcpyHostToDevice, stream));
+    const double* const* Vd = (const double* const*)ws.ptrs;
+    double* const* wd = ws.ptrs + nmem;
+    const int* jd = ws.jdev;
+    const int* one = ws.jdev + nmem;
+    double* h1 = ws.hdev;
+    double* h2 = ws.hdev + (size_t)nmem * ldp;
+    double* b2 = ws.hdev + 2 * (size_t)nmem * ldp;   // [nmem] spaced by ldp
+    const dim3 g(ws.grid, nmem);
+    const size_t sm = (size_t)jmax * sizeof(double);
+    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp);
+    k_gs_reduce_b<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, jd, h1);
+    k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h1, ldp);
+    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp);
+    k_gs_reduce_b<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, jd, h2);
+    k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h2, ldp);
+    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>((const double* const*)wd, n, n, one, (const double* const*)wd,
+                                             ws.partial, ldp);
+    k_gs_reduce_b<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, one, b2);
+    NS_LAUNCH_CHECK();
+    NS_CUDA(cudaMemcpyAsync(ws.hhost, ws.hdev, (size_t)3 * nmem * ldp * sizeof(double), cudaMemcpyDeviceToHost,
+                            stream));
+    NS_CUDA(cudaStreamSynchronize(stream));
+    for (int b = 0; b < nmem; ++b) {
+        if (j[b] < 0) continue;
+        for (int c = 0; c < j[b]; ++c)
+            h[(size_t)b * ldh + c] = ws.hhost[(size_t)b * ldp + c] + ws.hhost[(size_t)(nmem + b) * ldp + c];
+        beta[b] = std::sqrt(ws.hhost[(size_t)(2 * nmem + b) * ldp]);
+    }
+    return NSSTAB_OK;
+}
+
+// w[b] *= s[b] for members with a non-null w[b]
+int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream) {
+    NS_TRY(ws.alloc(nmem, 1));
+    std::vector<double*> ph(w, w + nmem);
+    NS_CUDA(cudaMemcpyAsync(ws.ptrs, ph.data(), nmem * sizeof(double*), cudaMemcpyHostToDevice, stream));
+    std::vector<double> sh(s, s + nmem);
+    NS_CUDA(cudaMemcpyAsync(ws.sdev, sh.data(), nmem * sizeof(double), cudaMemcpyHostToDevice, stream));
+    k_scale_b<<<dim3(ws.grid, nmem), kGsThreads, 0, stream>>>(ws.ptrs, n, ws.sdev);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
 int GsWork::alloc(int max_cols_) {
     if (max_cols_ <= max_cols) return NSSTAB_OK;
     release();

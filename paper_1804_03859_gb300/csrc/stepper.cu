@@ -35,6 +35,9 @@ enum RowMode { FWD_PLAIN = 0, FWD_RHS_NL = 1, FWD_RHS_LIN = 2, FWD_PEN_NL = 3, F
 
 template <class T> struct Fields {
     int nx, ny, nxh, logx, logy;
+    int bper;              // members per parameter set (member m uses set m / bper)
+    size_t fs, cs, ts;     // member strides: physical field, spectrum, operator table
+    const unsigned char* active;   // per-member flag: inactive members skip every kernel
     T idx2, idy2;          // 1/(2 dx), 1/(2 dy)
     T Uinf;
     T sfd_k1, sfd_k2;      // dt*chi_sfd, dt/Delta
@@ -49,6 +52,34 @@ template <class T> struct Fields {
     const T* tA; const T* tB; const T* tP;   // spectral operator tables [nxh+1][ny]
     const Cx<T>* twx; const Cx<T>* twy;      // twiddles exp(-2 pi i e/N)
 };
+
+// Offset the member-dependent pointers to member blockIdx.y (and its
+// parameter set).  Returns false for an inactive member: its blocks return
+// at once, so independent solves of a batch can drop out or idle.
+template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
+    const int m = blockIdx.y;
+    if (f.active && !f.active[m]) return false;
+    const int set = m / f.bper;
+    const size_t fo = (size_t)m * f.fs, co = (size_t)m * f.cs, so = (size_t)set * f.fs, to = (size_t)set * f.ts;
+    f.W += fo;
+    f.P += fo;
+    if (f.Y) f.Y += fo;
+    f.X1 += co;
+    f.X2 += co;
+    f.Wh += co;
+    f.Nh += co;
+    f.cS += so;
+    f.cG += so;
+    if (f.Ub) {
+        f.Ub += so;
+        f.Vb += so;
+        f.DxOb += so;
+        f.DyOb += so;
+    }
+    f.tA += to;
+    f.tB += to;
+    return true;
+}
 
 // ------------------------------------------------------------ point values
 
@@ -117,6 +148,7 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
 template <class T, int MODE, int LE>
 __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
     using C = Cx<T>;
+    if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int nx = f.nx, S = padded_len(nx);
@@ -158,9 +190,13 @@ __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_
 // (2p, 2p+1) of XA -> dA; otherwise pair p = row p of XA -> dA and row p of
 // XB -> dB.
 template <class T, int LE>
-__global__ void k_row_inverse(Fields<T> f, const Cx<T>* __restrict__ XA, const Cx<T>* __restrict__ XB,
-                              T* dA, T* dB, int RP, int logRP, bool same) {
+__global__ void k_row_inverse(Fields<T> f, int RP, int logRP, bool same) {
     using C = Cx<T>;
+    if (!member_view(f)) return;
+    const C* XA = same ? f.X2 : f.X1;
+    const C* XB = f.X2;
+    T* dA = same ? f.P : f.W;
+    T* dB = f.P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int nx = f.nx, ny = f.ny, nh = nx >> 1, S = padded_len(nx);
@@ -209,6 +245,7 @@ __device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
 template <class T, int LE>
 __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
     using C = Cx<T>;
+    if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int ny = f.ny, S = padded_len(ny), logy = f.logy;
@@ -253,6 +290,7 @@ __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
 template <class T, int LE>
 __global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
     using C = Cx<T>;
+    if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s1 = reinterpret_cast<C*>(smem_raw);
     const int ny = f.ny, S = padded_len(ny), logy = f.logy;
@@ -309,32 +347,52 @@ __global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
 
 // ------------------------------------------------------- pointwise kernels
 
+// Base-derived fields of parameter set blockIdx.y, from Omega_b and Psi_b held
+// in member slot blockIdx.y of W and P.
 template <class T>
 __global__ void k_base_fields(Fields<T> f, T* Ub, T* Vb, T* DxOb, T* DyOb) {
     const size_t n = (size_t)f.nx * f.ny;
+    const size_t off = (size_t)blockIdx.y * f.fs;
+    const T* P = f.P + off;   // Psi_b
+    const T* W = f.W + off;   // Omega_b
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(c & (f.nx - 1));
         const int j = (int)(c >> f.logx);
         const int ip = (i + 1) & (f.nx - 1), im = (i - 1) & (f.nx - 1);
         const int jp = (j + 1) & (f.ny - 1), jm = (j - 1) & (f.ny - 1);
-        const T* P = f.P;   // Psi_b
-        const T* W = f.W;   // Omega_b
-        Ub[c] = f.Uinf + (P[(size_t)jp * f.nx + i] - P[(size_t)jm * f.nx + i]) * f.idy2;
-        Vb[c] = -((P[(size_t)j * f.nx + ip] - P[(size_t)j * f.nx + im]) * f.idx2);
-        DxOb[c] = (W[(size_t)j * f.nx + ip] - W[(size_t)j * f.nx + im]) * f.idx2;
-        DyOb[c] = (W[(size_t)jp * f.nx + i] - W[(size_t)jm * f.nx + i]) * f.idy2;
+        Ub[off + c] = f.Uinf + (P[(size_t)jp * f.nx + i] - P[(size_t)jm * f.nx + i]) * f.idy2;
+        Vb[off + c] = -((P[(size_t)j * f.nx + ip] - P[(size_t)j * f.nx + im]) * f.idx2);
+        DxOb[off + c] = (W[(size_t)j * f.nx + ip] - W[(size_t)j * f.nx + im]) * f.idx2;
+        DyOb[off + c] = (W[(size_t)jp * f.nx + i] - W[(size_t)jm * f.nx + i]) * f.idy2;
     }
 }
 
-template <class A, class B>
-__global__ void k_convert(const A* __restrict__ src, B* __restrict__ dst, size_t n) {
+// dst[m] <- src[m] (FP64 -> T) for the members with a non-null source
+template <class T>
+__global__ void k_gather(const double* const* __restrict__ src, T* __restrict__ dst, size_t n, size_t fs) {
+    const double* s = src[blockIdx.y];
+    if (!s) return;
+    T* d = dst + (size_t)blockIdx.y * fs;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
-        dst[c] = (B)src[c];
+        d[c] = (T)s[c];
 }
 
-// partial[b] = sum over this block's share of (a - b)^2, accumulated in FP64
+// dst[m] <- src[m] (T -> FP64) for the members with a non-null destination
 template <class T>
-__global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, size_t n, double* partial) {
+__global__ void k_scatter(const T* __restrict__ src, double* const* __restrict__ dst, size_t n, size_t fs) {
+    double* d = dst[blockIdx.y];
+    if (!d) return;
+    const T* s = src + (size_t)blockIdx.y * fs;
+    for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x)
+        d[c] = (double)s[c];
+}
+
+// partial[m][b] = sum over block b's share of (a - b)^2 of member m, in FP64
+template <class T>
+__global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, size_t n, size_t fs, double* partial) {
+    a += (size_t)blockIdx.y * fs;
+    b += (size_t)blockIdx.y * fs;
+    partial += (size_t)blockIdx.y * gridDim.x;
     double acc = 0.0;
     for (size_t c = blockIdx.x * (size_t)blockDim.x + threadIdx.x; c < n; c += (size_t)gridDim.x * blockDim.x) {
         const double d = (double)a[c] - (double)b[c];
@@ -354,7 +412,7 @@ __global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, s
 // ------------------------------------------------------------- host side
 
 // One launch configuration: `per` sequences (row pairs or columns) per
-// block, 2^le elements per thread in the FFT passes.
+// block, 2^le elements per thread in the FFT passes; grid.y = members.
 struct Launch {
     int blocks = 0, threads = 0, per = 0, logper = 0, le = 3;
     size_t smem = 0;
@@ -365,23 +423,43 @@ struct Launch {
 enum KernelId { KCOLP = 0, KINVP = 1, KFWDR = 2, KCOLU = 3, KINVR = 4, KFWDP = 5 };
 template <class T> int max_threads_for(int kid, int le);
 
-static const int kRedBlocks = 256;
+static const int kRedBlocks = 64;           // partial sums per member
+static const int kPtBlocks = 152;           // grid.x of the pointwise kernels
 static const double kPi = 3.14159265358979323846;
 static const int kGraphChunk = 256;         // time steps per captured graph
 static const size_t kMaxSmem = 200 * 1024;
+
+#define K_FWD_PLAIN(le) k_row_forward<T, FWD_PLAIN, le>
+#define K_FWD_RNL(le) k_row_forward<T, FWD_RHS_NL, le>
+#define K_FWD_RLIN(le) k_row_forward<T, FWD_RHS_LIN, le>
+#define K_FWD_PNL(le) k_row_forward<T, FWD_PEN_NL, le>
+#define K_FWD_PLIN(le) k_row_forward<T, FWD_PEN_LIN, le>
+#define K_INV(le) k_row_inverse<T, le>
+#define K_COLP(le) k_col_poisson<T, le>
+#define K_COLU(le) k_col_update<T, le>
 
 template <class T>
 class StepperImpl : public StepperBase {
   public:
     using C = Cx<T>;
-    StepperImpl(const nsstab_config& cfg, cudaStream_t s) : cfg_(cfg), stream_(s) {}
+    StepperImpl(const nsstab_config& cfg, int nsets, const double* Re, const double* D, int per_set,
+                cudaStream_t s)
+        : cfg_(cfg), stream_(s), S_(nsets), bper_(per_set), B_(nsets * per_set) {
+        for (int k = 0; k < nsets; ++k) {
+            Re_.push_back(Re ? Re[k] : cfg.Re);
+            D_.push_back(D ? D[k] : cfg.cyl_D);
+        }
+    }
     ~StepperImpl() override { release(); }
 
     int init() override;
+    int members() const override { return B_; }
+    int sets() const override { return S_; }
     int poisson(const double* omega, double* psi) override;
     int step_nonlinear(double* omega, int nsteps) override;
     int set_base(const double* base_omega) override;
     int step_linear(const double* v_in, double* v_out, int nsteps) override;
+    int step_linear_ptrs(const double* const* in, double* const* out, int nsteps) override;
     int residual(const double* q, double* r) override;
     int sfd(double* omega, double chi, double Delta, double tol, long max_steps, int check_every,
             double* r, long* steps) override;
@@ -399,15 +477,23 @@ class StepperImpl : public StepperBase {
   private:
     nsstab_config cfg_;
     cudaStream_t stream_;
+    int S_, bper_, B_;
+    std::vector<double> Re_, D_;
     cudaStream_t cap_ = nullptr;   // private stream used only to capture graphs
     Fields<T> f_{};
     int nx_ = 0, ny_ = 0, nxh_ = 0;
-    size_t n_ = 0;
+    size_t n_ = 0, nc_ = 0;
     std::vector<void*> allocs_;
     T* Wsave_ = nullptr;
     C* Nhsave_ = nullptr;
-    double* red_ = nullptr;       // device partials
-    double* red_host_ = nullptr;  // pinned
+    double* red_ = nullptr;          // device partials [B][kRedBlocks]
+    double* red_host_ = nullptr;     // pinned
+    unsigned char* active_ = nullptr;
+    std::vector<unsigned char> active_host_;
+    const double** ptr_in_ = nullptr;   // device arrays of B member pointers
+    double** ptr_out_ = nullptr;
+    std::vector<const double*> pin_host_;
+    std::vector<double*> pout_host_;
     bool have_base_ = false;
     Launch plan_[kNumStepKernels];
     T scale_ = T(1);
@@ -447,15 +533,19 @@ class StepperImpl : public StepperBase {
     Launch default_plan(int kid) const;
     int set_smem_attr(int kid, const Launch& L);
 
+    int set_active(const std::vector<unsigned char>& a);
+    int all_active() { return set_active(std::vector<unsigned char>(B_, 1)); }
+    int gather(const double* const* src);                // W[m] <- src[m] (null: skip)
+    int scatter(const T* from, double* const* dst);      // dst[m] <- from[m] (null: skip)
+    int gather_contig(const double* src, int count);     // members 0..count-1 from [count][n]
+    int scatter_contig(const T* from, double* dst);      // all members to [B][n]
     int launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first);
     int launch_plain(cudaStream_t st);
-    int load(const double* src, T* dst);
-    int store(const T* src, double* dst);
     int transform_W();                                   // X1 = x-spectrum of W
     int stream_function(cudaStream_t st);                // Wh, X2, P from X1
     int issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last);
     int run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1 = true);
-    int sumsq_diff(const T* a, const T* b, double* out);
+    int sumsq_diff(const T* a, const T* b, double* out);   // out[B]
     int time_kernel(int kid, const Launch& L, int reps, float* ms);
 };
 
@@ -466,7 +556,7 @@ template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) co
     const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
     const int N = row ? nx_ : ny_;
     const int logN = row ? ilog2(nx_) : ilog2(ny_);
-    const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;   // sequences of the launch
+    const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;   // sequences per member
     const int nseq_smem = (kid == KCOLU) ? 2 : 1;                     // smem sequences per unit
     if (le < 1 || le > 3 || logN < le || per < 1 || !is_pow2(per) || per > count) return L;
     const int threads = per * (N >> le);
@@ -483,15 +573,15 @@ template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) co
 }
 
 // Default: the largest elements-per-thread (fewest FP64 operations per
-// point) that still gives every SM sub-partition a warp, then enough
-// sequences per block for at least two warps.
+// point) that still gives every SM sub-partition a warp over the whole
+// batch, then enough sequences per block for at least two warps.
 template <class T> Launch StepperImpl<T>::default_plan(int kid) const {
     const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
     const int N = row ? nx_ : ny_;
-    const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;
+    const long count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;
     const long target = 4L * 152 * 32;   // one warp per SM sub-partition
     int le = 3;
-    while (le > 2 && (long)count * (N >> le) < target) --le;
+    while (le > 2 && (long)B_ * count * (N >> le) < target) --le;
     if (ilog2(N) < le) le = ilog2(N);
     int per = 1;
     while (per * (N >> le) < 64 && 2 * per <= count) per *= 2;
@@ -510,14 +600,6 @@ template <class T> int StepperImpl<T>::set_smem_attr(int kid, const Launch& L) {
         case 2: NS_ATTR(KERNEL(2)); break; \
         default: NS_ATTR(KERNEL(3)); break; \
     }
-#define K_FWD_PLAIN(le) k_row_forward<T, FWD_PLAIN, le>
-#define K_FWD_RNL(le) k_row_forward<T, FWD_RHS_NL, le>
-#define K_FWD_RLIN(le) k_row_forward<T, FWD_RHS_LIN, le>
-#define K_FWD_PNL(le) k_row_forward<T, FWD_PEN_NL, le>
-#define K_FWD_PLIN(le) k_row_forward<T, FWD_PEN_LIN, le>
-#define K_INV(le) k_row_inverse<T, le>
-#define K_COLP(le) k_col_poisson<T, le>
-#define K_COLU(le) k_col_update<T, le>
     switch (kid) {
         case KCOLP: NS_ATTR_LE(K_COLP); break;
         case KINVP:
@@ -538,11 +620,11 @@ template <class T> int max_threads_for(int kid, int le) {
         if (cudaFuncGetAttributes(&a, fn) == cudaSuccess) m = std::min(m, a.maxThreadsPerBlock);
         else m = 0;
     };
-#define NS_TAKE_LE(KERNEL)                                  \
-    switch (le) {                                           \
-        case 1: take((const void*)KERNEL(1)); break;        \
-        case 2: take((const void*)KERNEL(2)); break;        \
-        default: take((const void*)KERNEL(3)); break;       \
+#define NS_TAKE_LE(KERNEL)                            \
+    switch (le) {                                     \
+        case 1: take((const void*)KERNEL(1)); break;  \
+        case 2: take((const void*)KERNEL(2)); break;  \
+        default: take((const void*)KERNEL(3)); break; \
     }
     switch (kid) {
         case KCOLP: NS_TAKE_LE(K_COLP); break;
@@ -565,8 +647,8 @@ template <class T> int StepperImpl<T>::set_plan(int kid, int le, int per) {
         set_error("set_plan: configuration not valid for this grid");
         return NSSTAB_ERR_INVALID_ARG;
     }
-    // the inverse-row kernel is shared by two launches: keep the larger smem attribute
     NS_TRY(set_smem_attr(kid, L));
+    // the inverse-row kernel serves two launches: keep the larger smem attribute
     if (kid == KINVP || kid == KINVR) {
         const Launch& o = plan_[kid == KINVP ? KINVR : KINVP];
         if (o.ok && o.le == L.le && o.smem > L.smem) NS_TRY(set_smem_attr(kid, o));
@@ -585,8 +667,8 @@ template <class T> int StepperImpl<T>::set_plan(int kid, int le, int per) {
 
 template <class T> int StepperImpl<T>::launch_plain(cudaStream_t st) {
     const Launch& L = plan_[KFWDR];
-#define CALL_PLAIN(le) \
-    k_row_forward<T, FWD_PLAIN, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+    const dim3 g(L.blocks, B_);
+#define CALL_PLAIN(le) k_row_forward<T, FWD_PLAIN, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
     NS_DISPATCH_LE(L, CALL_PLAIN);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
@@ -594,23 +676,21 @@ template <class T> int StepperImpl<T>::launch_plain(cudaStream_t st) {
 
 template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first) {
     const Launch& L = plan_[kid];
+    const dim3 g(L.blocks, B_);
     switch (kid) {
         case KCOLP: {
-#define CALL_COLP(le) k_col_poisson<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, scale_)
+#define CALL_COLP(le) k_col_poisson<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, scale_)
             NS_DISPATCH_LE(L, CALL_COLP);
             break;
         }
         case KINVP: {
-#define CALL_INVP(le) \
-    k_row_inverse<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, f_.X2, f_.X2, f_.P, f_.P, L.per, L.logper, true)
+#define CALL_INVP(le) k_row_inverse<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, true)
             NS_DISPATCH_LE(L, CALL_INVP);
             break;
         }
         case KFWDR: {
-#define CALL_FRL(le) \
-    k_row_forward<T, FWD_RHS_LIN, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
-#define CALL_FRN(le) \
-    k_row_forward<T, FWD_RHS_NL, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+#define CALL_FRL(le) k_row_forward<T, FWD_RHS_LIN, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+#define CALL_FRN(le) k_row_forward<T, FWD_RHS_NL, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
             if (linear) {
                 NS_DISPATCH_LE(L, CALL_FRL);
             } else {
@@ -620,21 +700,18 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
         }
         case KCOLU: {
             const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
-#define CALL_COLU(le) k_col_update<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, c1, c0, first)
+#define CALL_COLU(le) k_col_update<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, c1, c0, first)
             NS_DISPATCH_LE(L, CALL_COLU);
             break;
         }
         case KINVR: {
-#define CALL_INVR(le) \
-    k_row_inverse<T, le><<<L.blocks, L.threads, L.smem, st>>>(f_, f_.X1, f_.X2, f_.W, f_.P, L.per, L.logper, false)
+#define CALL_INVR(le) k_row_inverse<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false)
             NS_DISPATCH_LE(L, CALL_INVR);
             break;
         }
         default: {
-#define CALL_FPL(le) \
-    k_row_forward<T, FWD_PEN_LIN, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
-#define CALL_FPN(le) \
-    k_row_forward<T, FWD_PEN_NL, le><<<L.blocks, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
+#define CALL_FPL(le) k_row_forward<T, FWD_PEN_LIN, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
+#define CALL_FPN(le) k_row_forward<T, FWD_PEN_NL, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
             if (linear) {
                 NS_DISPATCH_LE(L, CALL_FPL);
             } else {
@@ -647,10 +724,12 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
     return NSSTAB_OK;
 }
 
+// --------------------------------------------------------------- tables
+
 template <class T> int StepperImpl<T>::build_tables() {
     const int nx = nx_, ny = ny_, nxh = nxh_;
     const double dx = cfg_.Lx / nx, dy = cfg_.Ly / ny;
-    const double nu = 1.0 / cfg_.Re, dt = cfg_.dt;
+    const double dt = cfg_.dt;
     const long double two_pi = 6.283185307179586476925286766559005768L;
     // twiddles exp(-2 pi i e / N) in extended precision, rounded once
     std::vector<C> twx(nx), twy(ny);
@@ -663,9 +742,9 @@ template <class T> int StepperImpl<T>::build_tables() {
         twy[e] = mk<T>((T)cosl(a), (T)(-sinl(a)));
     }
     // spectral operators over kx in [0, nx/2], ky in [0, ny): eigenvalue of
-    // the periodic 5-point Laplacian lam = lx(kx) + ly(ky)
+    // the periodic 5-point Laplacian lam = lx(kx) + ly(ky); tA, tB per set
     const size_t nt = (size_t)(nxh + 1) * ny;
-    std::vector<T> tA(nt), tB(nt), tP(nt);
+    std::vector<T> tA(nt * S_), tB(nt * S_), tP(nt);
     const double scale = 1.0 / ((double)nx * (double)ny);
     for (int kx = 0; kx <= nxh; ++kx) {
         const double sx = std::sin(kPi * kx / nx);
@@ -674,55 +753,62 @@ template <class T> int StepperImpl<T>::build_tables() {
             const double sy = std::sin(kPi * ky / ny);
             const double lam = lx - (4.0 / (dy * dy)) * sy * sy;
             const size_t g = (size_t)kx * ny + ky;
-            if (kx == 0 && ky == 0) {
-                tA[g] = tB[g] = tP[g] = T(0);
-                continue;
+            tP[g] = (kx == 0 && ky == 0) ? T(0) : (T)(-1.0 / lam);
+            for (int k = 0; k < S_; ++k) {
+                const double nu = 1.0 / Re_[k];
+                if (kx == 0 && ky == 0) {
+                    tA[k * nt + g] = tB[k * nt + g] = T(0);
+                    continue;
+                }
+                const double a = 1.0 + 0.5 * nu * dt * lam;
+                const double b = 1.0 - 0.5 * nu * dt * lam;
+                tA[k * nt + g] = (T)(scale * a / b);
+                tB[k * nt + g] = (T)(scale * dt / b);
             }
-            const double a = 1.0 + 0.5 * nu * dt * lam;
-            const double b = 1.0 - 0.5 * nu * dt * lam;
-            tA[g] = (T)(scale * a / b);
-            tB[g] = (T)(scale * dt / b);
-            tP[g] = (T)(-1.0 / lam);
         }
     }
-    // penalisation coefficients from the cylinder mask and the fringe
-    std::vector<T> cS(n_), cG(n_);
-    const double R = 0.5 * cfg_.cyl_D, w = 0.5 * cfg_.mask_cells * dx;
+    // penalisation coefficients from the cylinder mask and the fringe, per set
+    std::vector<T> cS(n_ * S_), cG(n_ * S_);
+    const double w = 0.5 * cfg_.mask_cells * dx;
     const double xs = (1.0 - cfg_.sponge_frac) * cfg_.Lx;
-    for (int j = 0; j < ny; ++j) {
-        const double y = j * dy;
-        for (int i = 0; i < nx; ++i) {
-            const double x = i * dx;
-            double chi = 0.0;
-            if (cfg_.cyl_D > 0.0) {
-                double ddx = std::fmod(x - cfg_.cyl_x + 0.5 * cfg_.Lx, cfg_.Lx);
-                if (ddx < 0) ddx += cfg_.Lx;
-                ddx -= 0.5 * cfg_.Lx;
-                double ddy = std::fmod(y - cfg_.cyl_y + 0.5 * cfg_.Ly, cfg_.Ly);
-                if (ddy < 0) ddy += cfg_.Ly;
-                ddy -= 0.5 * cfg_.Ly;
-                const double r = std::sqrt(ddx * ddx + ddy * ddy);
-                if (r <= R - w) chi = 1.0;
-                else if (r >= R + w) chi = 0.0;
-                else chi = 0.5 * (1.0 - std::sin(kPi * (r - R) / (2.0 * w)));
+    for (int k = 0; k < S_; ++k) {
+        const double Dk = D_[k], R = 0.5 * Dk;
+        for (int j = 0; j < ny; ++j) {
+            const double y = j * dy;
+            for (int i = 0; i < nx; ++i) {
+                const double x = i * dx;
+                double chi = 0.0;
+                if (Dk > 0.0) {
+                    double ddx = std::fmod(x - cfg_.cyl_x + 0.5 * cfg_.Lx, cfg_.Lx);
+                    if (ddx < 0) ddx += cfg_.Lx;
+                    ddx -= 0.5 * cfg_.Lx;
+                    double ddy = std::fmod(y - cfg_.cyl_y + 0.5 * cfg_.Ly, cfg_.Ly);
+                    if (ddy < 0) ddy += cfg_.Ly;
+                    ddy -= 0.5 * cfg_.Ly;
+                    const double r = std::sqrt(ddx * ddx + ddy * ddy);
+                    if (r <= R - w) chi = 1.0;
+                    else if (r >= R + w) chi = 0.0;
+                    else chi = 0.5 * (1.0 - std::sin(kPi * (r - R) / (2.0 * w)));
+                }
+                double sig = 0.0;
+                if (cfg_.sponge_sigma > 0.0 && cfg_.sponge_frac > 0.0 && x >= xs) {
+                    const double sn = std::sin(kPi * (x - xs) / (cfg_.sponge_frac * cfg_.Lx));
+                    sig = cfg_.sponge_sigma * sn * sn;
+                }
+                const double s = dt * (chi / cfg_.eta + sig);
+                const size_t c = k * n_ + (size_t)j * nx + i;
+                cS[c] = (T)(s / (1.0 + s));
+                cG[c] = (T)(dt * sig * cfg_.Uinf / (1.0 + s));
             }
-            double sig = 0.0;
-            if (cfg_.sponge_sigma > 0.0 && cfg_.sponge_frac > 0.0 && x >= xs) {
-                const double sn = std::sin(kPi * (x - xs) / (cfg_.sponge_frac * cfg_.Lx));
-                sig = cfg_.sponge_sigma * sn * sn;
-            }
-            const double s = dt * (chi / cfg_.eta + sig);
-            cS[(size_t)j * nx + i] = (T)(s / (1.0 + s));
-            cG[(size_t)j * nx + i] = (T)(dt * sig * cfg_.Uinf / (1.0 + s));
         }
     }
     NS_CUDA(cudaMemcpyAsync((void*)f_.twx, twx.data(), nx * sizeof(C), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaMemcpyAsync((void*)f_.twy, twy.data(), ny * sizeof(C), cudaMemcpyHostToDevice, stream_));
-    NS_CUDA(cudaMemcpyAsync((void*)f_.tA, tA.data(), nt * sizeof(T), cudaMemcpyHostToDevice, stream_));
-    NS_CUDA(cudaMemcpyAsync((void*)f_.tB, tB.data(), nt * sizeof(T), cudaMemcpyHostToDevice, stream_));
-    NS_CUDA(cudaMemcpyAsync((void*)f_.tP, tP.data(), nt * sizeof(T), cudaMemcpyHostToDevice, stream_));
-    NS_CUDA(cudaMemcpyAsync((void*)f_.cS, cS.data(), n_ * sizeof(T), cudaMemcpyHostToDevice, stream_));
-    NS_CUDA(cudaMemcpyAsync((void*)f_.cG, cG.data(), n_ * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.tA, tA.data(), tA.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.tB, tB.data(), tB.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.tP, tP.data(), tP.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.cS, cS.data(), cS.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    NS_CUDA(cudaMemcpyAsync((void*)f_.cG, cG.data(), cG.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaStreamSynchronize(stream_));   // host vectors go out of scope
     return NSSTAB_OK;
 }
@@ -732,49 +818,58 @@ template <class T> int StepperImpl<T>::init() {
     ny_ = cfg_.ny;
     nxh_ = nx_ / 2;
     n_ = (size_t)nx_ * ny_;
-    const size_t nc = (size_t)nxh_ * ny_;
+    nc_ = (size_t)nxh_ * ny_;
+    const size_t nt = (size_t)(nxh_ + 1) * ny_;
     f_.nx = nx_;
     f_.ny = ny_;
     f_.nxh = nxh_;
     f_.logx = ilog2(nx_);
     f_.logy = ilog2(ny_);
+    f_.bper = bper_;
+    f_.fs = n_;
+    f_.cs = nc_;
+    f_.ts = nt;
     f_.idx2 = (T)(1.0 / (2.0 * cfg_.Lx / nx_));
     f_.idy2 = (T)(1.0 / (2.0 * cfg_.Ly / ny_));
     f_.Uinf = (T)cfg_.Uinf;
     scale_ = (T)(1.0 / ((double)nx_ * (double)ny_));
+    const size_t B = B_, S = S_;
     T *W, *P, *cS, *cG, *tA, *tB, *tP;
     C *X1, *X2, *Wh, *Nh, *twx, *twy;
-    const size_t nt = (size_t)(nxh_ + 1) * ny_;
-    NS_TRY(dalloc(&W, n_));
-    NS_TRY(dalloc(&P, n_));
-    NS_TRY(dalloc(&cS, n_));
-    NS_TRY(dalloc(&cG, n_));
-    NS_TRY(dalloc(&X1, nc));
-    NS_TRY(dalloc(&X2, nc));
-    NS_TRY(dalloc(&Wh, nc));
-    NS_TRY(dalloc(&Nh, nc));
-    NS_TRY(dalloc(&tA, nt));
-    NS_TRY(dalloc(&tB, nt));
+    NS_TRY(dalloc(&W, B * n_));
+    NS_TRY(dalloc(&P, B * n_));
+    NS_TRY(dalloc(&X1, B * nc_));
+    NS_TRY(dalloc(&X2, B * nc_));
+    NS_TRY(dalloc(&Wh, B * nc_));
+    NS_TRY(dalloc(&Nh, B * nc_));
+    NS_TRY(dalloc(&cS, S * n_));
+    NS_TRY(dalloc(&cG, S * n_));
+    NS_TRY(dalloc(&tA, S * nt));
+    NS_TRY(dalloc(&tB, S * nt));
     NS_TRY(dalloc(&tP, nt));
     NS_TRY(dalloc(&twx, (size_t)nx_));
     NS_TRY(dalloc(&twy, (size_t)ny_));
-    NS_TRY(dalloc(&red_, (size_t)kRedBlocks));
-    NS_CUDA(cudaMallocHost((void**)&red_host_, kRedBlocks * sizeof(double)));
+    NS_TRY(dalloc(&red_, B * kRedBlocks));
+    NS_TRY(dalloc(&active_, B));
+    NS_TRY(dalloc(&ptr_in_, B));
+    NS_TRY(dalloc(&ptr_out_, B));
+    NS_CUDA(cudaMallocHost((void**)&red_host_, B * kRedBlocks * sizeof(double)));
     f_.W = W; f_.P = P; f_.cS = cS; f_.cG = cG;
     f_.X1 = X1; f_.X2 = X2; f_.Wh = Wh; f_.Nh = Nh;
     f_.tA = tA; f_.tB = tB; f_.tP = tP;
     f_.twx = twx; f_.twy = twy;
     f_.Y = nullptr;
     f_.Ub = f_.Vb = f_.DxOb = f_.DyOb = nullptr;
+    f_.active = active_;
     NS_TRY(build_tables());
-
     // zero the workspace so that timing runs of the autotuner see finite data
-    NS_CUDA(cudaMemsetAsync(f_.W, 0, n_ * sizeof(T), stream_));
-    NS_CUDA(cudaMemsetAsync(f_.P, 0, n_ * sizeof(T), stream_));
-    NS_CUDA(cudaMemsetAsync(f_.X1, 0, nc * sizeof(C), stream_));
-    NS_CUDA(cudaMemsetAsync(f_.X2, 0, nc * sizeof(C), stream_));
-    NS_CUDA(cudaMemsetAsync(f_.Wh, 0, nc * sizeof(C), stream_));
-    NS_CUDA(cudaMemsetAsync(f_.Nh, 0, nc * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.W, 0, B * n_ * sizeof(T), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.P, 0, B * n_ * sizeof(T), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.X1, 0, B * nc_ * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.X2, 0, B * nc_ * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.Wh, 0, B * nc_ * sizeof(C), stream_));
+    NS_CUDA(cudaMemsetAsync(f_.Nh, 0, B * nc_ * sizeof(C), stream_));
+    NS_TRY(all_active());
     NS_CUDA(cudaStreamCreateWithFlags(&cap_, cudaStreamNonBlocking));
     for (int k = 0; k < kNumStepKernels; ++k) {
         const Launch L = default_plan(k);
@@ -788,25 +883,45 @@ template <class T> int StepperImpl<T>::init() {
     return NSSTAB_OK;
 }
 
-template <class T> int StepperImpl<T>::load(const double* src, T* dst) {
-    if (sizeof(T) == sizeof(double)) {
-        NS_CUDA(cudaMemcpyAsync(dst, src, n_ * sizeof(double), cudaMemcpyDeviceToDevice, stream_));
-    } else {
-        k_convert<double, T><<<304, 256, 0, stream_>>>(src, dst, n_);
-        NS_LAUNCH_CHECK();
-    }
+// ------------------------------------------------- member data movement
+
+// Host vectors are pageable: cudaMemcpyAsync stages them before returning,
+// so they may be reused by the next call at once.
+template <class T> int StepperImpl<T>::set_active(const std::vector<unsigned char>& a) {
+    active_host_ = a;
+    NS_CUDA(cudaMemcpyAsync(active_, active_host_.data(), B_, cudaMemcpyHostToDevice, stream_));
     return NSSTAB_OK;
 }
 
-template <class T> int StepperImpl<T>::store(const T* src, double* dst) {
-    if (sizeof(T) == sizeof(double)) {
-        NS_CUDA(cudaMemcpyAsync(dst, src, n_ * sizeof(double), cudaMemcpyDeviceToDevice, stream_));
-    } else {
-        k_convert<T, double><<<304, 256, 0, stream_>>>(src, dst, n_);
-        NS_LAUNCH_CHECK();
-    }
+template <class T> int StepperImpl<T>::gather(const double* const* src) {
+    pin_host_.assign(src, src + B_);
+    NS_CUDA(cudaMemcpyAsync(ptr_in_, pin_host_.data(), B_ * sizeof(double*), cudaMemcpyHostToDevice, stream_));
+    k_gather<T><<<dim3(kPtBlocks, B_), 256, 0, stream_>>>(ptr_in_, f_.W, n_, n_);
+    NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
+
+template <class T> int StepperImpl<T>::scatter(const T* from, double* const* dst) {
+    pout_host_.assign(dst, dst + B_);
+    NS_CUDA(cudaMemcpyAsync(ptr_out_, pout_host_.data(), B_ * sizeof(double*), cudaMemcpyHostToDevice, stream_));
+    k_scatter<T><<<dim3(kPtBlocks, B_), 256, 0, stream_>>>(from, ptr_out_, n_, n_);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::gather_contig(const double* src, int count) {
+    std::vector<const double*> p(B_, nullptr);
+    for (int m = 0; m < count; ++m) p[m] = src + (size_t)m * n_;
+    return gather(p.data());
+}
+
+template <class T> int StepperImpl<T>::scatter_contig(const T* from, double* dst) {
+    std::vector<double*> p(B_);
+    for (int m = 0; m < B_; ++m) p[m] = dst + (size_t)m * n_;
+    return scatter(from, p.data());
+}
+
+// ------------------------------------------------------------- stepping
 
 template <class T> int StepperImpl<T>::transform_W() { return launch_plain(stream_); }
 
@@ -833,7 +948,8 @@ int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool s
 // Run nsteps steps on the stepper's stream.  Long runs replay CUDA graphs of
 // up to kGraphChunk steps, captured once per (length, flags) on a private
 // stream and launched into the stepper's stream; the AB2 history carries
-// from one chunk to the next through the workspace.
+// from one chunk to the next through the workspace.  The active-member mask
+// is read from device memory at run time, so graphs serve any subset.
 template <class T> int StepperImpl<T>::run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1) {
     if (linear && !have_base_) {
         set_error("linearised step requested before a base flow was set");
@@ -894,9 +1010,10 @@ template <class T> int StepperImpl<T>::time_kernel(int kid, const Launch& L, int
 }
 
 // Measure every valid (elements per thread, sequences per block) pair of
-// each kernel on this grid and keep the fastest.  Clobbers the workspace
-// (never the base flow).  chosen[2k], chosen[2k+1] = (le, per) of kernel k.
+// each kernel on this grid and batch and keep the fastest.  Clobbers the
+// workspace (never the base flow).  chosen[2k], chosen[2k+1] = (le, per).
 template <class T> int StepperImpl<T>::autotune(int reps, int* chosen) {
+    NS_TRY(all_active());
     for (int kid = 0; kid < kNumStepKernels; ++kid) {
         Launch best = plan_[kid];
         float best_ms = 1e30f;
@@ -933,7 +1050,8 @@ template <class T> int StepperImpl<T>::profile_linear(const double* v, int nstep
     cudaEvent_t ev[kNumStepKernels + 1];
     for (int k = 0; k <= kNumStepKernels; ++k) NS_CUDA(cudaEventCreate(&ev[k]));
     for (int k = 0; k < kNumStepKernels; ++k) ms[k] = 0.0;
-    int rc = load(v, f_.W);
+    int rc = all_active();
+    if (rc == NSSTAB_OK) rc = gather_contig(v, B_);
     if (rc == NSSTAB_OK) rc = transform_W();
     for (int s = 0; s < nsteps && rc == NSSTAB_OK; ++s) {
         const bool first = (s == 0);
@@ -960,70 +1078,98 @@ template <class T> int StepperImpl<T>::profile_linear(const double* v, int nstep
 }
 
 template <class T> int StepperImpl<T>::poisson(const double* omega, double* psi) {
-    NS_TRY(load(omega, f_.W));
+    NS_TRY(all_active());
+    NS_TRY(gather_contig(omega, B_));
     NS_TRY(transform_W());
     NS_TRY(stream_function(stream_));
-    return store(f_.P, psi);
+    return scatter_contig(f_.P, psi);
 }
 
 template <class T> int StepperImpl<T>::step_nonlinear(double* omega, int nsteps) {
-    NS_TRY(load(omega, f_.W));
+    NS_TRY(all_active());
+    NS_TRY(gather_contig(omega, B_));
     if (nsteps > 0) {
         NS_TRY(transform_W());
         NS_TRY(run_steps(nsteps, false, false, false));
     }
-    return store(f_.W, omega);
+    return scatter_contig(f_.W, omega);
 }
 
 template <class T> int StepperImpl<T>::set_base(const double* base_omega) {
     if (!f_.Ub) {
         T *Ub, *Vb, *DxOb, *DyOb;
-        NS_TRY(dalloc(&Ub, n_));
-        NS_TRY(dalloc(&Vb, n_));
-        NS_TRY(dalloc(&DxOb, n_));
-        NS_TRY(dalloc(&DyOb, n_));
+        NS_TRY(dalloc(&Ub, (size_t)S_ * n_));
+        NS_TRY(dalloc(&Vb, (size_t)S_ * n_));
+        NS_TRY(dalloc(&DxOb, (size_t)S_ * n_));
+        NS_TRY(dalloc(&DyOb, (size_t)S_ * n_));
         f_.Ub = Ub; f_.Vb = Vb; f_.DxOb = DxOb; f_.DyOb = DyOb;
         clear_graphs();   // captured kernels carry the field pointers by value
     }
-    NS_TRY(load(base_omega, f_.W));
+    // the S base flows go through member slots 0..S-1
+    std::vector<unsigned char> a(B_, 0);
+    for (int k = 0; k < S_; ++k) a[k] = 1;
+    NS_TRY(set_active(a));
+    NS_TRY(gather_contig(base_omega, S_));
     NS_TRY(transform_W());
     NS_TRY(stream_function(stream_));   // P = Psi_b
-    k_base_fields<T><<<304, 256, 0, stream_>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb, (T*)f_.DyOb);
+    k_base_fields<T><<<dim3(kPtBlocks, S_), 256, 0, stream_>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb, (T*)f_.DyOb);
     NS_LAUNCH_CHECK();
+    NS_TRY(all_active());
     have_base_ = true;
     return NSSTAB_OK;
 }
 
 template <class T> int StepperImpl<T>::step_linear(const double* v_in, double* v_out, int nsteps) {
-    NS_TRY(load(v_in, f_.W));
+    std::vector<const double*> pi(B_);
+    std::vector<double*> po(B_);
+    for (int m = 0; m < B_; ++m) {
+        pi[m] = v_in + (size_t)m * n_;
+        po[m] = v_out + (size_t)m * n_;
+    }
+    return step_linear_ptrs(pi.data(), po.data(), nsteps);
+}
+
+template <class T> int StepperImpl<T>::step_linear_ptrs(const double* const* in, double* const* out, int nsteps) {
+    if (!have_base_) {
+        set_error("linearised step requested before a base flow was set");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    std::vector<unsigned char> a(B_);
+    for (int m = 0; m < B_; ++m) a[m] = in[m] != nullptr;
+    NS_TRY(set_active(a));
+    NS_TRY(gather(in));
     if (nsteps > 0) {
         NS_TRY(transform_W());
         NS_TRY(run_steps(nsteps, true, false, false));
     }
-    return store(f_.W, v_out);
+    return scatter(f_.W, out);
 }
 
 template <class T> int StepperImpl<T>::sumsq_diff(const T* a, const T* b, double* out) {
-    k_diff_sumsq<T><<<kRedBlocks, 256, 0, stream_>>>(a, b, n_, red_);
+    k_diff_sumsq<T><<<dim3(kRedBlocks, B_), 256, 0, stream_>>>(a, b, n_, n_, red_);
     NS_LAUNCH_CHECK();
-    NS_CUDA(cudaMemcpyAsync(red_host_, red_, kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost, stream_));
+    NS_CUDA(cudaMemcpyAsync(red_host_, red_, (size_t)B_ * kRedBlocks * sizeof(double), cudaMemcpyDeviceToHost,
+                            stream_));
     NS_CUDA(cudaStreamSynchronize(stream_));
-    double s = 0.0;
-    for (int b2 = 0; b2 < kRedBlocks; ++b2) s += red_host_[b2];
-    *out = s;
+    for (int m = 0; m < B_; ++m) {
+        double s = 0.0;
+        for (int b2 = 0; b2 < kRedBlocks; ++b2) s += red_host_[(size_t)m * kRedBlocks + b2];
+        out[m] = s;
+    }
     return NSSTAB_OK;
 }
 
 template <class T> int StepperImpl<T>::residual(const double* q, double* r) {
-    if (!Wsave_) NS_TRY(dalloc(&Wsave_, n_));
-    NS_TRY(load(q, f_.W));
-    NS_CUDA(cudaMemcpyAsync(Wsave_, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+    if (!Wsave_) NS_TRY(dalloc(&Wsave_, (size_t)B_ * n_));
+    NS_TRY(all_active());
+    NS_TRY(gather_contig(q, B_));
+    NS_CUDA(cudaMemcpyAsync(Wsave_, f_.W, (size_t)B_ * n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
     NS_TRY(transform_W());
     NS_TRY(run_steps(1, false, false, false));
-    double ss = 0.0;
-    NS_TRY(sumsq_diff(f_.W, Wsave_, &ss));
+    std::vector<double> ss(B_);
+    NS_TRY(sumsq_diff(f_.W, Wsave_, ss.data()));
     const double dx = cfg_.Lx / nx_, dy = cfg_.Ly / ny_;
-    *r = std::sqrt(ss * dx * dy) / cfg_.dt;
+    for (int m = 0; m < B_; ++m) r[m] = std::sqrt(ss[m] * dx * dy) / cfg_.dt;
     return NSSTAB_OK;
 }
 
@@ -1032,24 +1178,23 @@ int StepperImpl<T>::sfd(double* omega, double chi, double Delta, double tol, lon
                         double* r_out, long* steps_out) {
     if (!f_.Y) {
         T* Y;
-        NS_TRY(dalloc(&Y, n_));
+        NS_TRY(dalloc(&Y, (size_t)B_ * n_));
         f_.Y = Y;
     }
-    if (!Wsave_) NS_TRY(dalloc(&Wsave_, n_));
-    if (!Nhsave_) NS_TRY(dalloc(&Nhsave_, (size_t)nxh_ * ny_));
-    const T k1 = (T)(cfg_.dt * chi), k2 = (T)(cfg_.dt / Delta);
-    f_.sfd_k1 = k1;
-    f_.sfd_k2 = k2;
+    if (!Wsave_) NS_TRY(dalloc(&Wsave_, (size_t)B_ * n_));
+    if (!Nhsave_) NS_TRY(dalloc(&Nhsave_, (size_t)B_ * nc_));
+    f_.sfd_k1 = (T)(cfg_.dt * chi);
+    f_.sfd_k2 = (T)(cfg_.dt / Delta);
     clear_graphs();   // captured kernels carry the gains and the Y pointer by value
-    NS_TRY(load(omega, f_.W));
-    NS_CUDA(cudaMemcpyAsync(f_.Y, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+    NS_TRY(all_active());
+    NS_TRY(gather_contig(omega, B_));
+    NS_CUDA(cudaMemcpyAsync(f_.Y, f_.W, (size_t)B_ * n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
     NS_TRY(transform_W());
     const double dx = cfg_.Lx / nx_, dy = cfg_.Ly / ny_;
     long k = 0;
-    double r = INFINITY;
+    std::vector<double> r(B_, INFINITY), ss(B_);
     int status = NSSTAB_NOT_CONVERGED;
     bool first_chunk = true;
-    const size_t nc = (size_t)nxh_ * ny_;
     while (k < max_steps) {
         const long chunk = std::min<long>(check_every, max_steps - k);
         // the AB2 history continues across chunks: only the very first step is AB1
@@ -1057,27 +1202,31 @@ int StepperImpl<T>::sfd(double* omega, double chi, double Delta, double tol, lon
         first_chunk = false;
         k += chunk;
         // residual of the current X with one plain AB1 step, then restore the state
-        NS_CUDA(cudaMemcpyAsync(Wsave_, f_.W, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
-        NS_CUDA(cudaMemcpyAsync(Nhsave_, f_.Nh, nc * sizeof(C), cudaMemcpyDeviceToDevice, stream_));
+        NS_CUDA(cudaMemcpyAsync(Wsave_, f_.W, (size_t)B_ * n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+        NS_CUDA(cudaMemcpyAsync(Nhsave_, f_.Nh, (size_t)B_ * nc_ * sizeof(C), cudaMemcpyDeviceToDevice, stream_));
         NS_TRY(run_steps(1, false, false, false));
-        double ss = 0.0;
-        NS_TRY(sumsq_diff(f_.W, Wsave_, &ss));
-        r = std::sqrt(ss * dx * dy) / cfg_.dt;
-        NS_CUDA(cudaMemcpyAsync(f_.W, Wsave_, n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
-        NS_CUDA(cudaMemcpyAsync(f_.Nh, Nhsave_, nc * sizeof(C), cudaMemcpyDeviceToDevice, stream_));
+        NS_TRY(sumsq_diff(f_.W, Wsave_, ss.data()));
+        bool all_ok = true, finite = true;
+        for (int m = 0; m < B_; ++m) {
+            r[m] = std::sqrt(ss[m] * dx * dy) / cfg_.dt;
+            finite = finite && std::isfinite(r[m]);
+            all_ok = all_ok && r[m] <= tol;
+        }
+        NS_CUDA(cudaMemcpyAsync(f_.W, Wsave_, (size_t)B_ * n_ * sizeof(T), cudaMemcpyDeviceToDevice, stream_));
+        NS_CUDA(cudaMemcpyAsync(f_.Nh, Nhsave_, (size_t)B_ * nc_ * sizeof(C), cudaMemcpyDeviceToDevice, stream_));
         NS_TRY(transform_W());
-        if (!std::isfinite(r)) {
+        if (!finite) {
             status = NSSTAB_DIVERGED;
             break;
         }
-        if (r <= tol) {
+        if (all_ok) {
             status = NSSTAB_OK;
             break;
         }
     }
-    NS_TRY(store(f_.W, omega));
+    NS_TRY(scatter_contig(f_.W, omega));
     NS_CUDA(cudaStreamSynchronize(stream_));
-    *r_out = r;
+    for (int m = 0; m < B_; ++m) r_out[m] = r[m];
     *steps_out = k;
     return status;
 }
@@ -1097,9 +1246,10 @@ int validate_config(const nsstab_config& c) {
     return NSSTAB_OK;
 }
 
-StepperBase* make_stepper(const nsstab_config& cfg, cudaStream_t stream) {
-    if (cfg.precision == 32) return new StepperImpl<float>(cfg, stream);
-    return new StepperImpl<double>(cfg, stream);
+StepperBase* make_stepper(const nsstab_config& cfg, int nsets, const double* Re, const double* D, int per_set,
+                          cudaStream_t stream) {
+    if (cfg.precision == 32) return new StepperImpl<float>(cfg, nsets, Re, D, per_set, stream);
+    return new StepperImpl<double>(cfg, nsets, Re, D, per_set, stream);
 }
 
 }  // namespace nsstab

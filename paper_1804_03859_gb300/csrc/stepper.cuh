@@ -7,14 +7,25 @@ namespace nsstab {
 
 // Precision-independent face of a stepper; StepperImpl<T> implements it for
 // T = double (FP64 stepper) and T = float (FP32 stepper with FP64 I/O).
+//
+// A stepper advances a batch of B = S * per_set members on one grid: member
+// m belongs to parameter set m / per_set (its own Reynolds number and
+// cylinder diameter, and its own base flow for the linearised step).  Field
+// arguments are [B][ny][nx] (base flows [S][ny][nx]); a single stepper is
+// the batch B = S = 1.
 struct StepperBase {
     virtual ~StepperBase() {}
     virtual int init() = 0;
+    virtual int members() const = 0;
+    virtual int sets() const = 0;
     virtual int poisson(const double* omega, double* psi) = 0;
     virtual int step_nonlinear(double* omega, int nsteps) = 0;
     virtual int set_base(const double* base_omega) = 0;
     virtual int step_linear(const double* v_in, double* v_out, int nsteps) = 0;
-    virtual int residual(const double* q, double* r) = 0;
+    // per-member device pointers (host arrays of B); a null input pointer
+    // leaves that member out of this call
+    virtual int step_linear_ptrs(const double* const* in, double* const* out, int nsteps) = 0;
+    virtual int residual(const double* q, double* r) = 0;   // r: host [B]
     virtual int sfd(double* omega, double chi, double Delta, double tol, long max_steps,
                     int check_every, double* r, long* steps) = 0;
     virtual int launches_per_step() const = 0;
@@ -30,7 +41,8 @@ struct StepperBase {
 
 constexpr int kNumStepKernels = 6;   // col_poisson, row_inverse(psi), row_forward(rhs),
                                      // col_update, row_inverse(omega*, psi*), row_forward(pen)
-StepperBase* make_stepper(const nsstab_config& cfg, cudaStream_t stream);
+StepperBase* make_stepper(const nsstab_config& cfg, int nsets, const double* Re, const double* D, int per_set,
+                          cudaStream_t stream);
 int validate_config(const nsstab_config& cfg);
 
 // Krylov helpers (krylov_kernels.cu), all FP64 on `stream`.
@@ -45,6 +57,22 @@ struct GsWork {
 };
 int cgs2(const double* V, long ldv, long n, int j, double* w, double* h, double* beta,
          GsWork& ws, cudaStream_t stream);
+
+// Workspace of the batched Gram-Schmidt kernels (one member per grid.y).
+struct GsBatch {
+    double* partial = nullptr;   // [B][grid][max_cols]
+    double* hdev = nullptr;      // h1, h2, beta^2: [3][B][max_cols]
+    double* hhost = nullptr;     // pinned copy of hdev
+    double* sdev = nullptr;      // [B] scale factors
+    int* jdev = nullptr;         // [2][B] column counts
+    double** ptrs = nullptr;     // [2][B] member pointers
+    int B = 0, max_cols = 0, grid = 0;
+    int alloc(int nmem, int cols);
+    void release();
+};
+int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j, double* const* w,
+               double* h, int ldh, double* beta, GsBatch& ws, cudaStream_t stream);
+int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream);
 int vec_norm(const double* x, long n, double* out, GsWork& ws, cudaStream_t stream);
 int vec_scale(double* dst, const double* src, long n, double s, cudaStream_t stream);
 // out[:, c] = sum_k V[:, k] C[k, c] for c < p (C: device, column-major

@@ -46,6 +46,9 @@ class Config(ctypes.Structure):
 SIGNATURES = [
     ("nsstab_config_default", None, [ctypes.POINTER(Config)]),
     ("stepper_create", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("batch_create", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, _dp, _dp, ctypes.c_int, ctypes.c_void_p,
+                                    ctypes.POINTER(ctypes.c_void_p)]),
+    ("stepper_members", ctypes.c_int, [ctypes.c_void_p, _ip, _ip]),
     ("stepper_destroy", None, [ctypes.c_void_p]),
     ("stepper_poisson", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("step_nonlinear", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
@@ -57,6 +60,9 @@ SIGNATURES = [
     ("arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                     ctypes.c_void_p, _ip, _ip, _ip]),
+    ("batch_arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                          _dp, ctypes.c_void_p, _ip, _ip, _ip]),
     ("stepper_profile_linear", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, _dp]),
     ("stepper_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     ("stepper_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -228,18 +234,46 @@ class EigResult:
 
 
 class Stepper:
-    """Owner of one ``nsstab_stepper`` bound to the current torch stream."""
+    """Owner of one ``nsstab_stepper`` bound to the current torch stream.
 
-    def __init__(self, **cfg):
+    ``Stepper(**cfg)`` is a single stepper; ``Stepper(Re=[...], cyl_D=[...],
+    per_set=b, **cfg)`` with a list of Reynolds numbers (and optionally of
+    diameters) is a batch of len(Re) * b members (``batch_create``): field
+    arguments are then [B, ny, nx] tensors and base flows [S, ny, nx].
+    """
+
+    def __init__(self, per_set: int = 1, **cfg):
         import torch
 
         if not torch.cuda.is_available():
             raise RuntimeError("nsstab needs a CUDA GPU")
+        Re = cfg.pop("Re", None)
+        D = cfg.pop("cyl_D", None)
+        batched = np.ndim(Re) == 1 or np.ndim(D) == 1 or per_set != 1
+        if not batched:
+            if Re is not None:
+                cfg["Re"] = Re
+            if D is not None:
+                cfg["cyl_D"] = D
         self.cfg = _cfg_from(**cfg)
         self.shape = (self.cfg.ny, self.cfg.nx)
         self._stream = torch.cuda.current_stream()
-        self._h = stepper_create(self.cfg, self._stream.cuda_stream)
         self._lib = load_library()
+        if not batched:
+            self._h = stepper_create(self.cfg, self._stream.cuda_stream)
+            self.members, self.sets = 1, 1
+            return
+        nsets = len(Re) if np.ndim(Re) == 1 else (len(D) if np.ndim(D) == 1 else 1)
+        re = np.ascontiguousarray(np.broadcast_to(self.cfg.Re if Re is None else Re, (nsets,)), dtype=np.float64)
+        dd = np.ascontiguousarray(np.broadcast_to(self.cfg.cyl_D if D is None else D, (nsets,)), dtype=np.float64)
+        h = ctypes.c_void_p()
+        _check(self._lib.batch_create(ctypes.byref(self.cfg), nsets, re.ctypes.data_as(_dp), dd.ctypes.data_as(_dp),
+                                      int(per_set), ctypes.c_void_p(self._stream.cuda_stream), ctypes.byref(h)),
+               "batch_create")
+        self._h = h
+        mem, sets = ctypes.c_int(), ctypes.c_int()
+        _check(self._lib.stepper_members(self._h, ctypes.byref(mem), ctypes.byref(sets)), "stepper_members")
+        self.members, self.sets = mem.value, sets.value
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -252,8 +286,12 @@ class Stepper:
         except Exception:
             pass
 
-    def _p(self, t, name):
-        return _field_ptr(t, self.shape, name)
+    def _p(self, t, name, count=None):
+        count = self.members if count is None else count
+        p = _field_ptr(t, self.shape, name)
+        if t.numel() != count * self.shape[0] * self.shape[1]:
+            raise ValueError(f"{name} must hold {count} fields of shape {self.shape}")
+        return p
 
     def stepper_poisson(self, omega, psi):
         _check(self._lib.stepper_poisson(self._h, self._p(omega, "omega"), self._p(psi, "psi")), "stepper_poisson")
@@ -262,26 +300,53 @@ class Stepper:
         _check(self._lib.step_nonlinear(self._h, self._p(omega, "omega"), int(nsteps)), "step_nonlinear")
 
     def stepper_set_base(self, base):
-        _check(self._lib.stepper_set_base(self._h, self._p(base, "base")), "stepper_set_base")
+        _check(self._lib.stepper_set_base(self._h, self._p(base, "base", self.sets)), "stepper_set_base")
 
     def apply_expTL(self, base, v_in, v_out, T: float):
-        bp = self._p(base, "base") if base is not None else None
+        bp = self._p(base, "base", self.sets) if base is not None else None
         _check(self._lib.apply_expTL(self._h, bp, self._p(v_in, "v_in"), self._p(v_out, "v_out"), float(T)),
                "apply_expTL")
 
-    def stepper_residual(self, q) -> float:
-        r = ctypes.c_double()
-        _check(self._lib.stepper_residual(self._h, self._p(q, "q"), ctypes.byref(r)), "stepper_residual",
+    def stepper_residual(self, q):
+        """Base-flow residual r(q); a float for a single stepper, an array for a batch."""
+        r = np.zeros(self.members)
+        _check(self._lib.stepper_residual(self._h, self._p(q, "q"), r.ctypes.data_as(_dp)), "stepper_residual",
                allow_soft=True)
-        return r.value
+        return float(r[0]) if self.members == 1 else r
 
     def sfd_baseflow(self, omega, chi: float, Delta: float, tol: float, max_steps: int, check_every: int = 100):
-        r = ctypes.c_double()
+        r = np.zeros(self.members)
         steps = ctypes.c_long()
         rc = _check(self._lib.sfd_baseflow(self._h, self._p(omega, "omega"), float(chi), float(Delta), float(tol),
-                                           int(max_steps), int(check_every), ctypes.byref(r), ctypes.byref(steps)),
+                                           int(max_steps), int(check_every), r.ctypes.data_as(_dp),
+                                           ctypes.byref(steps)),
                     "sfd_baseflow", allow_soft=True)
-        return rc, r.value, steps.value
+        return rc, (float(r[0]) if self.members == 1 else r), steps.value
+
+    def batch_arnoldi_eigs(self, bases, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
+                           eigvecs=None) -> list:
+        """One eigenproblem per member (batched stepper): a list of EigResult."""
+        B = self.members
+        re, im, res = (np.zeros((B, nev + 1)) for _ in range(3))
+        n_eig, n_conv, n_mv = (np.zeros(B, dtype=np.int32) for _ in range(3))
+        bp = self._p(bases, "bases", self.sets) if bases is not None else None
+        ev = None
+        if eigvecs is not None:
+            if eigvecs.numel() != B * (nev + 1) * self.shape[0] * self.shape[1]:
+                raise ValueError("eigvecs must hold B * (nev + 1) fields")
+            ev = _field_ptr(eigvecs, self.shape, "eigvecs")
+        ip = lambda a: a.ctypes.data_as(_ip)
+        rc = _check(self._lib.batch_arnoldi_eigs(self._h, bp, self._p(v0, "v0"), int(m), int(nev), float(tol),
+                                                 int(max_restarts), float(T), re.ctypes.data_as(_dp),
+                                                 im.ctypes.data_as(_dp), res.ctypes.data_as(_dp), ev, ip(n_eig),
+                                                 ip(n_conv), ip(n_mv)),
+                    "batch_arnoldi_eigs", allow_soft=True)
+        out = []
+        for b in range(B):
+            k = int(n_eig[b])
+            status = OK if n_conv[b] >= k else NOT_CONVERGED
+            out.append(EigResult(re[b, :k] + 1j * im[b, :k], res[b, :k], int(n_conv[b]), int(n_mv[b]), status))
+        return out
 
     def arnoldi_eigs(self, base, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
                      eigvecs=None) -> EigResult:
@@ -304,7 +369,7 @@ class Stepper:
     KERNELS = ("col_poisson", "row_inverse_psi", "row_forward_rhs", "col_update", "row_inverse_star",
                "row_forward_pen")
 
-    def stepper_profile_linear(self, v, nsteps: int) -> dict:
+    def stepper_profile_linear(self, v, nsteps: int) -> dict:  # noqa: D401
         """Per-kernel milliseconds (summed over nsteps linearised steps)."""
         ms = np.zeros(6)
         _check(self._lib.stepper_profile_linear(self._h, self._p(v, "v"), int(nsteps), ms.ctypes.data_as(_dp)),
