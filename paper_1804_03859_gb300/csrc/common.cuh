@@ -46,6 +46,29 @@ template <class C, class T> __device__ __forceinline__ C cscale(C a, T s) { C r;
 template <class C> __device__ __forceinline__ C cmul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
 template <class C> __device__ __forceinline__ C cmul_pi(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
 
+// two adjacent complex values as one access (16 B for float, two 16-B
+// halves of one 32-B sector for double)
+template <class T> struct PairIO;
+template <> struct PairIO<float> {
+    __device__ static __forceinline__ void load(const float2* p, float2& a, float2& b) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        a.x = v.x; a.y = v.y; b.x = v.z; b.y = v.w;
+    }
+    __device__ static __forceinline__ void store(float2* p, float2 a, float2 b) {
+        *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+template <> struct PairIO<double> {
+    __device__ static __forceinline__ void load(const double2* p, double2& a, double2& b) {
+        a = p[0];
+        b = p[1];
+    }
+    __device__ static __forceinline__ void store(double2* p, double2 a, double2 b) {
+        p[0] = a;
+        p[1] = b;
+    }
+};
+
 // --------------------------------------------------------------- errors
 void set_error(const std::string& msg);
 const char* last_error();

@@ -11,21 +11,57 @@
 // output are both in natural order and no bit reversal is needed.
 //
 // Shared-memory layout: sequence f occupies S = padded_len(N) (or more)
-// slots starting at s + f*S; element e sits at slot pad8(e) = e + e/8, which
+// slots starting at s + f*S; element e sits at slot sw<T>(e) = e + e/8, which
 // keeps the stride-8 stores of the first pass free of bank conflicts.
 //
-// Twiddles come from a precomputed table tw[e] = exp(-2 pi i e / Nt) of the
-// longest transform length Nt of the grid (computed on the host in extended
-// precision), read through the read-only cache: on GB300 the FP64 pipe is
-// the scarce resource, so no sine or cosine is evaluated on the device.
+// Twiddles come from precomputed per-pass tables (twiddle_table_len; built
+// on the host in extended precision) read through the read-only cache: on
+// GB300 the FP64 pipe is the scarce resource, so no sine or cosine is
+// evaluated on the device, and each butterfly's twiddles are one contiguous
+// row so that the loads of a warp are coalesced.
 #pragma once
 
 #include "common.cuh"
 
 namespace nsstab {
 
-__host__ __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
-__host__ __device__ constexpr int padded_len(int n) { return n + (n >> 3); }
+// Shared-memory slot of element i of a sequence: an XOR swizzle inside each
+// 128-byte bank row (16 float2 or 8 double2 elements) that keeps both the
+// unit-stride accesses and the stride-8 stores of the first radix-8 pass
+// free of bank conflicts, without padding.
+template <class T> __device__ __forceinline__ int sw(int i);
+template <> __device__ __forceinline__ int sw<float>(int i) { return i ^ ((i >> 4) & 15); }
+template <> __device__ __forceinline__ int sw<double>(int i) { return i ^ ((i >> 3) & 7); }
+__host__ __device__ constexpr int padded_len(int n) { return n; }
+// Distance (in elements) between consecutive sequences in shared memory.
+// When `rp` sequences share one shared-memory wavefront (element-interleaved
+// staging loops, or short sequences several to a warp), their starts are
+// spread over the 32 four-byte banks, 32/rp banks apart.  elem_words =
+// element size / 4 bytes.
+__host__ __device__ inline int seq_stride(int n, int rp, int elem_words) {
+    int s = n;
+    if (rp <= 1) return s;
+    const int target = (32 / rp) & 31;
+    for (int i = 0; i < 32; ++i, ++s)
+        if (((s * elem_words) & 31) == target) return s;
+    return n + 1;
+}
+
+// Twiddle tables, one per elements-per-thread choice LE: for every pass
+// with Stockham stride Ns and radix R (in the order fft_smem runs them), R
+// rows of Ns entries exp(-2 pi i r k / (Ns R)), r < R, k < Ns.  Consecutive
+// threads of a pass have consecutive k, so the loads of a warp for one r
+// are contiguous.  Length < 2N.
+inline int twiddle_table_len(int logN, int LE) {
+    int len = 0, nsl = 0, rem = logN;
+    while (rem >= LE) {
+        len += (1 << nsl) << LE;
+        nsl += LE;
+        rem -= LE;
+    }
+    if (rem > 0) len += (1 << nsl) << rem;
+    return len;
+}
 
 template <class T> struct Consts;
 template <> struct Consts<double> { static constexpr double rsqrt2 = 0.70710678118654752440084436210485; };
@@ -89,14 +125,14 @@ template <bool INV, class T, int LR> __device__ __forceinline__ void dft_r(Cx<T>
 // W_N^(r k N/(Ns R)).
 template <bool INV, class T, int LE, int LR>
 __device__ __forceinline__ void stockham_pass(Cx<T>* d, int q, int lq, int logN, int nsl,
-                                              const Cx<T>* __restrict__ tw, int twshift, bool act) {
+                                              const Cx<T>* __restrict__ tw, bool act) {
     constexpr int E = 1 << LE, R = 1 << LR, U = E / R;
     Cx<T> v[E];
     if (act) {
 #pragma unroll
         for (int u = 0; u < U; ++u)
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[u * R + r] = d[pad8(q + (u << lq) + (r << (logN - LR)))];
+            for (int r = 0; r < R; ++r) v[u * R + r] = d[sw<T>(q + (u << lq) + (r << (logN - LR)))];
     }
     __syncthreads();
     if (act) {
@@ -105,14 +141,13 @@ __device__ __forceinline__ void stockham_pass(Cx<T>* d, int q, int lq, int logN,
             const int b = q + (u << lq);
             const int k = b & ((1 << nsl) - 1);
             if (nsl > 0) {
-                const int sh = logN - nsl - LR + twshift;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[u * R + r] = twiddle<INV, T>(v[u * R + r], tw, (r * k) << sh);
+                for (int r = 1; r < R; ++r) v[u * R + r] = twiddle<INV, T>(v[u * R + r], tw, (r << nsl) + k);
             }
             dft_r<INV, T, LR>(v + u * R);
             const int base = ((b - k) << LR) + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) d[pad8(base + (r << nsl))] = v[u * R + r];
+            for (int r = 0; r < R; ++r) d[sw<T>(base + (r << nsl))] = v[u * R + r];
         }
     }
     __syncthreads();
@@ -121,10 +156,10 @@ __device__ __forceinline__ void stockham_pass(Cx<T>* d, int q, int lq, int logN,
 // In-place transform of nseq sequences (see file comment).  All threads of
 // the block must call it.  Every thread owns E = 2^LE elements per pass:
 // radix-E passes, then one smaller radix for the remaining factors.
-// Requirements: logN >= LE; blockDim.x * E is a multiple of N; twshift =
-// log2(Nt / N) for the table tw of length Nt.
+// Requirements: logN >= LE; blockDim.x * E is a multiple of N; tw is the
+// twiddle table of this N and LE (twiddle_table_len entries).
 template <bool INV, class T, int LE>
-__device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __restrict__ tw, int twshift) {
+__device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __restrict__ tw) {
     const int t = threadIdx.x;
     const int lq = logN - LE;                   // log2(N/E): threads per sequence
     const int q = t & ((1 << lq) - 1);
@@ -135,13 +170,15 @@ __device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __res
         Cx<T>* d = s + (size_t)(act ? f : 0) * S;
         int nsl = 0;
         int rem = logN;
+        const Cx<T>* twp = tw;   // start of this pass's rows
         while (rem >= LE) {
-            stockham_pass<INV, T, LE, LE>(d, q, lq, logN, nsl, tw, twshift, act);
+            stockham_pass<INV, T, LE, LE>(d, q, lq, logN, nsl, twp, act);
+            twp += (1 << nsl) << LE;
             nsl += LE;
             rem -= LE;
         }
-        if (LE == 3 && rem == 2) stockham_pass<INV, T, LE, (LE == 3 ? 2 : 1)>(d, q, lq, logN, nsl, tw, twshift, act);
-        if (rem == 1) stockham_pass<INV, T, LE, 1>(d, q, lq, logN, nsl, tw, twshift, act);
+        if (LE == 3 && rem == 2) stockham_pass<INV, T, LE, (LE == 3 ? 2 : 1)>(d, q, lq, logN, nsl, twp, act);
+        if (rem == 1) stockham_pass<INV, T, LE, 1>(d, q, lq, logN, nsl, twp, act);
     }
 }
 

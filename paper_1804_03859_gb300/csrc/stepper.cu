@@ -50,7 +50,7 @@ template <class T> struct Fields {
     Cx<T>* X1; Cx<T>* X2;  // x-spectral, y-physical [kx][y]
     Cx<T>* Wh; Cx<T>* Nh;  // full spectra [kx][ky]
     const T* tA; const T* tB; const T* tP;   // spectral operator tables [nxh+1][ny]
-    const Cx<T>* twx; const Cx<T>* twy;      // twiddles exp(-2 pi i e/N)
+    const Cx<T>* twx[4]; const Cx<T>* twy[4];   // per-pass twiddle tables for LE = 1, 2, 3
 };
 
 // Offset the member-dependent pointers to member blockIdx.y (and its
@@ -80,6 +80,22 @@ template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
     f.tB += to;
     return true;
 }
+
+// Diagonal operators at (kx, ky), kx in [0, nx/2]: Crank-Nicolson A = a/b,
+// B = dt/b (both times the 1/(nx ny) of the inverse transform) and the
+// inverse Laplacian P = -1/lam (zero for the mean mode), read from tables
+// computed on the host in FP64 and rounded once to the stepper's precision
+// (a division costs ~10 FP64 instructions on GB300, and evaluating them in
+// FP32 on the device adds several roundings that show in the FP32
+// eigenvalues).
+template <class T> struct SpecOp {
+    __device__ static __forceinline__ void ab(const Fields<T>& f, int kx, int ky, T& A, T& B) {
+        const size_t g = (size_t)kx * f.ny + ky;
+        A = f.tA[g];
+        B = f.tB[g];
+    }
+    __device__ static __forceinline__ T p(const Fields<T>& f, int kx, int ky) { return f.tP[(size_t)kx * f.ny + ky]; }
+};
 
 // ------------------------------------------------------------ point values
 
@@ -145,24 +161,28 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
 
 // Forward x-transform of RP row pairs per block, with the row values made by
 // MODE.  Writes the packed half-spectra to X1 ([kx][y]) when do_fft.
+// Register budget: blocks of up to 512 threads at 8 elements per thread (the
+// largest rows, nx = 4096, need 512), up to 1024 otherwise.
+#define NS_FFT_BOUNDS __launch_bounds__(LE == 3 ? 512 : 1024)
+
 template <class T, int MODE, int LE>
-__global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
+__global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
     using C = Cx<T>;
     if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int nx = f.nx, S = padded_len(nx);
+    const int nx = f.nx, S = seq_stride(nx, RP, (int)sizeof(C) / 4);
     const int pair0 = blockIdx.x * RP;
     for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
         const int p = e >> f.logx, i = e & (nx - 1);
         const int j0 = 2 * (pair0 + p);
         const T a = row_value<T, MODE>(f, i, j0, sfd);
         const T b = row_value<T, MODE>(f, i, j0 + 1, sfd);
-        s[p * S + pad8(i)] = mk<T>(a, b);
+        s[p * S + sw<T>(i)] = mk<T>(a, b);
     }
     if (!do_fft) return;
     __syncthreads();
-    fft_smem<false, T, LE>(s, f.logx, S, RP, f.twx, 0);
+    fft_smem<false, T, LE>(s, f.logx, S, RP, f.twx[LE]);
     // split Z = FFT(a + i b) into the half-spectra of a and b
     const int nh = nx >> 1;
     for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
@@ -171,18 +191,16 @@ __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_
         const C* z = s + p * S;
         C A, B;
         if (k == 0) {
-            const C z0 = z[0], zn = z[pad8(nh)];
+            const C z0 = z[0], zn = z[sw<T>(nh)];
             A = mk<T>(z0.x, zn.x);
             B = mk<T>(z0.y, zn.y);
         } else {
-            const C zk = z[pad8(k)];
-            const C zm = cconj(z[pad8(nx - k)]);
+            const C zk = z[sw<T>(k)];
+            const C zm = cconj(z[sw<T>(nx - k)]);
             A = cscale(cadd(zk, zm), T(0.5));
             B = cscale(cmul_mi(csub(zk, zm)), T(0.5));
         }
-        C* out = f.X1 + (size_t)k * f.ny + j0;
-        out[0] = A;
-        out[1] = B;
+        PairIO<T>::store(f.X1 + (size_t)k * f.ny + j0, A, B);   // rows j0, j0+1 are adjacent
     }
 }
 
@@ -190,7 +208,7 @@ __global__ void k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_
 // (2p, 2p+1) of XA -> dA; otherwise pair p = row p of XA -> dA and row p of
 // XB -> dB.
 template <class T, int LE>
-__global__ void k_row_inverse(Fields<T> f, int RP, int logRP, bool same) {
+__global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP, bool same) {
     using C = Cx<T>;
     if (!member_view(f)) return;
     const C* XA = same ? f.X2 : f.X1;
@@ -199,32 +217,36 @@ __global__ void k_row_inverse(Fields<T> f, int RP, int logRP, bool same) {
     T* dB = f.P;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int nx = f.nx, ny = f.ny, nh = nx >> 1, S = padded_len(nx);
+    const int nx = f.nx, ny = f.ny, nh = nx >> 1, S = seq_stride(nx, RP, (int)sizeof(C) / 4);
     const int pair0 = blockIdx.x * RP;
     for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
         const int p = e & (RP - 1), k = e >> logRP;
         const int pr = pair0 + p;
         const int ra = same ? 2 * pr : pr;
-        const int rb = same ? 2 * pr + 1 : pr;
-        const C A = XA[(size_t)k * ny + ra];
-        const C B = (same ? XA : XB)[(size_t)k * ny + rb];
+        C A, B;
+        if (same) {
+            PairIO<T>::load(XA + (size_t)k * ny + ra, A, B);       // rows 2pr, 2pr+1 are adjacent
+        } else {
+            A = XA[(size_t)k * ny + ra];
+            B = XB[(size_t)k * ny + ra];
+        }
         C* z = s + p * S;
         if (k == 0) {
             z[0] = mk<T>(A.x, B.x);
-            z[pad8(nh)] = mk<T>(A.y, B.y);
+            z[sw<T>(nh)] = mk<T>(A.y, B.y);
         } else {
-            z[pad8(k)] = mk<T>(A.x - B.y, A.y + B.x);        // A + i B
-            z[pad8(nx - k)] = mk<T>(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
+            z[sw<T>(k)] = mk<T>(A.x - B.y, A.y + B.x);        // A + i B
+            z[sw<T>(nx - k)] = mk<T>(A.x + B.y, B.x - A.y);   // conj(A) + i conj(B)
         }
     }
     __syncthreads();
-    fft_smem<true, T, LE>(s, f.logx, S, RP, f.twx, 0);
+    fft_smem<true, T, LE>(s, f.logx, S, RP, f.twx[LE]);
     for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
         const int p = e >> f.logx, i = e & (nx - 1);
         const int pr = pair0 + p;
         const int ra = same ? 2 * pr : pr;
         const int rb = same ? 2 * pr + 1 : pr;
-        const C z = s[p * S + pad8(i)];
+        const C z = s[p * S + sw<T>(i)];
         dA[(size_t)ra * nx + i] = z.x;
         (same ? dA : dB)[(size_t)rb * nx + i] = z.y;
     }
@@ -243,22 +265,23 @@ __device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
 // Forward y-transform of CP columns of X1, store Wh, psi^ = scale * tP * omega^,
 // inverse y-transform into X2.
 template <class T, int LE>
-__global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
+__global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     using C = Cx<T>;
     if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
-    const int ny = f.ny, S = padded_len(ny), logy = f.logy;
+    const int ny = f.ny, logy = f.logy;
+    const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
     const int c0 = blockIdx.x * CP;
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
-        s[c * S + pad8(j)] = f.X1[(size_t)(c0 + c) * ny + j];
+        s[c * S + sw<T>(j)] = f.X1[(size_t)(c0 + c) * ny + j];
     }
     __syncthreads();
-    fft_smem<false, T, LE>(s, logy, S, CP, f.twy, 0);
+    fft_smem<false, T, LE>(s, logy, S, CP, f.twy[LE]);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, k = e & (ny - 1);
-        f.Wh[(size_t)(c0 + c) * ny + k] = s[c * S + pad8(k)];
+        f.Wh[(size_t)(c0 + c) * ny + k] = s[c * S + sw<T>(k)];
     }
     __syncthreads();
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
@@ -266,20 +289,20 @@ __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
         const int kx = c0 + c;
         C* z = s + c * S;
         if (kx != 0) {
-            z[pad8(k)] = cscale(z[pad8(k)], scale * f.tP[(size_t)kx * ny + k]);
+            z[sw<T>(k)] = cscale(z[sw<T>(k)], scale * SpecOp<T>::p(f, kx, k));
         } else if (k <= (ny >> 1)) {
             const int km = (ny - k) & (ny - 1);
-            const T f0 = scale * f.tP[k], fN = scale * f.tP[(size_t)f.nxh * ny + k];
-            const C zk = z[pad8(k)], zm = z[pad8(km)];
-            z[pad8(k)] = apply_packed0(zk, cconj(zm), f0, fN);
-            if (km != k) z[pad8(km)] = apply_packed0(zm, cconj(zk), f0, fN);
+            const T f0 = scale * SpecOp<T>::p(f, 0, k), fN = scale * SpecOp<T>::p(f, f.nxh, k);
+            const C zk = z[sw<T>(k)], zm = z[sw<T>(km)];
+            z[sw<T>(k)] = apply_packed0(zk, cconj(zm), f0, fN);
+            if (km != k) z[sw<T>(km)] = apply_packed0(zm, cconj(zk), f0, fN);
         }
     }
     __syncthreads();
-    fft_smem<true, T, LE>(s, logy, S, CP, f.twy, 0);
+    fft_smem<true, T, LE>(s, logy, S, CP, f.twy[LE]);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
-        f.X2[(size_t)(c0 + c) * ny + j] = s[c * S + pad8(j)];
+        f.X2[(size_t)(c0 + c) * ny + j] = s[c * S + sw<T>(j)];
     }
 }
 
@@ -288,60 +311,73 @@ __global__ void k_col_poisson(Fields<T> f, int CP, T scale) {
 // (tA, tB carry the 1/(nx ny) of the inverse transform); Nh <- N^n; inverse
 // y-transforms of omega*^ -> X1 and psi*^ -> X2.
 template <class T, int LE>
-__global__ void k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
+__global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
     using C = Cx<T>;
     if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s1 = reinterpret_cast<C*>(smem_raw);
-    const int ny = f.ny, S = padded_len(ny), logy = f.logy;
-    C* s2 = s1 + (size_t)CP * S;
+    const int ny = f.ny, logy = f.logy;
+    const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
+    C* s2 = s1 + (size_t)CP * S;   // omega^ in, psi*^ out
+    C* s3 = s2 + (size_t)CP * S;   // N^{n-1} in
     const int c0i = blockIdx.x * CP;
+    // all three input columns are read at once (one wait for the whole block)
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
-        s1[c * S + pad8(j)] = f.X1[(size_t)(c0i + c) * ny + j];
+        const size_t g = (size_t)(c0i + c) * ny + j;
+        s1[c * S + sw<T>(j)] = f.X1[g];
+        s2[c * S + sw<T>(j)] = f.Wh[g];
+        if (!first) s3[c * S + sw<T>(j)] = f.Nh[g];
     }
     __syncthreads();
-    fft_smem<false, T, LE>(s1, logy, S, CP, f.twy, 0);
+    fft_smem<false, T, LE>(s1, logy, S, CP, f.twy[LE]);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, k = e & (ny - 1);
         const int kx = c0i + c;
         const size_t g = (size_t)kx * ny + k;
+        C* z1 = s1 + c * S;
+        C* z2 = s2 + c * S;
+        const C* z3 = s3 + c * S;
         if (kx != 0) {
-            const C nn = s1[c * S + pad8(k)];
-            const C r = first ? cscale(nn, c1) : cadd(cscale(nn, c1), cscale(f.Nh[g], c0));
+            const C nn = z1[sw<T>(k)];
+            const C r = first ? cscale(nn, c1) : cadd(cscale(nn, c1), cscale(z3[sw<T>(k)], c0));
             f.Nh[g] = nn;
-            const C ws = cadd(cscale(f.Wh[g], f.tA[g]), cscale(r, f.tB[g]));
-            s1[c * S + pad8(k)] = ws;
-            s2[c * S + pad8(k)] = cscale(ws, f.tP[g]);
+            T A, B;
+            SpecOp<T>::ab(f, kx, k, A, B);
+            const C ws = cadd(cscale(z2[sw<T>(k)], A), cscale(r, B));
+            z1[sw<T>(k)] = ws;
+            z2[sw<T>(k)] = cscale(ws, SpecOp<T>::p(f, kx, k));
         } else if (k <= (ny >> 1)) {
             const int km = (ny - k) & (ny - 1);
-            const size_t gN = (size_t)f.nxh * ny;
-            const C nk = s1[pad8(k)], nm = s1[pad8(km)];
+            const C nk = z1[sw<T>(k)], nm = z1[sw<T>(km)];
             C rk = cscale(nk, c1), rm = cscale(nm, c1);
             if (!first) {
-                rk = cadd(rk, cscale(f.Nh[k], c0));
-                rm = cadd(rm, cscale(f.Nh[km], c0));
+                rk = cadd(rk, cscale(z3[sw<T>(k)], c0));
+                rm = cadd(rm, cscale(z3[sw<T>(km)], c0));
             }
             f.Nh[k] = nk;
             f.Nh[km] = nm;
-            const C wk = f.Wh[k], wm = f.Wh[km];
-            const C wsk = cadd(apply_packed0(wk, cconj(wm), f.tA[k], f.tA[gN + k]),
-                               apply_packed0(rk, cconj(rm), f.tB[k], f.tB[gN + k]));
-            const C wsm = cadd(apply_packed0(wm, cconj(wk), f.tA[km], f.tA[gN + km]),
-                               apply_packed0(rm, cconj(rk), f.tB[km], f.tB[gN + km]));
-            s1[pad8(k)] = wsk;
-            s1[pad8(km)] = wsm;
-            s2[pad8(k)] = apply_packed0(wsk, cconj(wsm), f.tP[k], f.tP[gN + k]);
-            s2[pad8(km)] = apply_packed0(wsm, cconj(wsk), f.tP[km], f.tP[gN + km]);
+            T A0k, B0k, ANk, BNk, A0m, B0m, ANm, BNm;
+            SpecOp<T>::ab(f, 0, k, A0k, B0k);
+            SpecOp<T>::ab(f, f.nxh, k, ANk, BNk);
+            SpecOp<T>::ab(f, 0, km, A0m, B0m);
+            SpecOp<T>::ab(f, f.nxh, km, ANm, BNm);
+            const C wk = z2[sw<T>(k)], wm = z2[sw<T>(km)];
+            const C wsk = cadd(apply_packed0(wk, cconj(wm), A0k, ANk), apply_packed0(rk, cconj(rm), B0k, BNk));
+            const C wsm = cadd(apply_packed0(wm, cconj(wk), A0m, ANm), apply_packed0(rm, cconj(rk), B0m, BNm));
+            z1[sw<T>(k)] = wsk;
+            z1[sw<T>(km)] = wsm;
+            z2[sw<T>(k)] = apply_packed0(wsk, cconj(wsm), SpecOp<T>::p(f, 0, k), SpecOp<T>::p(f, f.nxh, k));
+            z2[sw<T>(km)] = apply_packed0(wsm, cconj(wsk), SpecOp<T>::p(f, 0, km), SpecOp<T>::p(f, f.nxh, km));
         }
     }
     __syncthreads();
-    fft_smem<true, T, LE>(s1, logy, S, 2 * CP, f.twy, 0);
+    fft_smem<true, T, LE>(s1, logy, S, 2 * CP, f.twy[LE]);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
         const size_t g = (size_t)(c0i + c) * ny + j;
-        f.X1[g] = s1[c * S + pad8(j)];
-        f.X2[g] = s2[c * S + pad8(j)];
+        f.X1[g] = s1[c * S + sw<T>(j)];
+        f.X2[g] = s2[c * S + sw<T>(j)];
     }
 }
 
@@ -557,10 +593,11 @@ template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) co
     const int N = row ? nx_ : ny_;
     const int logN = row ? ilog2(nx_) : ilog2(ny_);
     const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;   // sequences per member
-    const int nseq_smem = (kid == KCOLU) ? 2 : 1;                     // smem sequences per unit
+    const int nseq_smem = (kid == KCOLU) ? 3 : 1;                     // smem sequences per unit
     if (le < 1 || le > 3 || logN < le || per < 1 || !is_pow2(per) || per > count) return L;
     const int threads = per * (N >> le);
-    const size_t smem = (size_t)per * nseq_smem * padded_len(N) * sizeof(C);
+    const int rp = row ? per : ((N >> le) < 32 ? 32 / (N >> le) : 1);
+    const size_t smem = (size_t)per * nseq_smem * seq_stride(N, rp, (int)sizeof(C) / 4) * sizeof(C);
     if (threads > 1024 || smem > kMaxSmem) return L;
     L.per = per;
     L.logper = ilog2(per);
@@ -731,16 +768,24 @@ template <class T> int StepperImpl<T>::build_tables() {
     const double dx = cfg_.Lx / nx, dy = cfg_.Ly / ny;
     const double dt = cfg_.dt;
     const long double two_pi = 6.283185307179586476925286766559005768L;
-    // twiddles exp(-2 pi i e / N) in extended precision, rounded once
-    std::vector<C> twx(nx), twy(ny);
-    for (int e = 0; e < nx; ++e) {
-        long double a = two_pi * (long double)e / (long double)nx;
-        twx[e] = mk<T>((T)cosl(a), (T)(-sinl(a)));
-    }
-    for (int e = 0; e < ny; ++e) {
-        long double a = two_pi * (long double)e / (long double)ny;
-        twy[e] = mk<T>((T)cosl(a), (T)(-sinl(a)));
-    }
+    // per-pass twiddle tables (see fft.cuh) in extended precision, rounded once
+    auto build_tw = [&](int N, int LE, std::vector<C>& out) {
+        const int logN = ilog2(N);
+        out.clear();
+        int nsl = 0, rem = logN;
+        auto pass = [&](int LR) {
+            const int Ns = 1 << nsl, R = 1 << LR;
+            for (int r = 0; r < R; ++r)
+                for (int k = 0; k < Ns; ++k) {
+                    const long double a = two_pi * (long double)(r * k) / (long double)(Ns * R);
+                    out.push_back(mk<T>((T)cosl(a), (T)(-sinl(a))));
+                }
+            nsl += LR;
+            rem -= LR;
+        };
+        while (rem >= LE) pass(LE);
+        if (rem > 0) pass(rem);
+    };
     // spectral operators over kx in [0, nx/2], ky in [0, ny): eigenvalue of
     // the periodic 5-point Laplacian lam = lx(kx) + ly(ky); tA, tB per set
     const size_t nt = (size_t)(nxh + 1) * ny;
@@ -802,8 +847,17 @@ template <class T> int StepperImpl<T>::build_tables() {
             }
         }
     }
-    NS_CUDA(cudaMemcpyAsync((void*)f_.twx, twx.data(), nx * sizeof(C), cudaMemcpyHostToDevice, stream_));
-    NS_CUDA(cudaMemcpyAsync((void*)f_.twy, twy.data(), ny * sizeof(C), cudaMemcpyHostToDevice, stream_));
+    for (int le = 1; le <= 3; ++le) {
+        std::vector<C> tx, ty;
+        if (ilog2(nx) >= le) {
+            build_tw(nx, le, tx);
+            NS_CUDA(cudaMemcpy((void*)f_.twx[le], tx.data(), tx.size() * sizeof(C), cudaMemcpyHostToDevice));
+        }
+        if (ilog2(ny) >= le) {
+            build_tw(ny, le, ty);
+            NS_CUDA(cudaMemcpy((void*)f_.twy[le], ty.data(), ty.size() * sizeof(C), cudaMemcpyHostToDevice));
+        }
+    }
     NS_CUDA(cudaMemcpyAsync((void*)f_.tA, tA.data(), tA.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaMemcpyAsync((void*)f_.tB, tB.data(), tB.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaMemcpyAsync((void*)f_.tP, tP.data(), tP.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
@@ -835,7 +889,7 @@ template <class T> int StepperImpl<T>::init() {
     scale_ = (T)(1.0 / ((double)nx_ * (double)ny_));
     const size_t B = B_, S = S_;
     T *W, *P, *cS, *cG, *tA, *tB, *tP;
-    C *X1, *X2, *Wh, *Nh, *twx, *twy;
+    C *X1, *X2, *Wh, *Nh;
     NS_TRY(dalloc(&W, B * n_));
     NS_TRY(dalloc(&P, B * n_));
     NS_TRY(dalloc(&X1, B * nc_));
@@ -847,8 +901,15 @@ template <class T> int StepperImpl<T>::init() {
     NS_TRY(dalloc(&tA, S * nt));
     NS_TRY(dalloc(&tB, S * nt));
     NS_TRY(dalloc(&tP, nt));
-    NS_TRY(dalloc(&twx, (size_t)nx_));
-    NS_TRY(dalloc(&twy, (size_t)ny_));
+    for (int le = 1; le <= 3; ++le) {
+        C *tx, *ty;
+        NS_TRY(dalloc(&tx, (size_t)2 * nx_));
+        NS_TRY(dalloc(&ty, (size_t)2 * ny_));
+        f_.twx[le] = tx;
+        f_.twy[le] = ty;
+    }
+    f_.twx[0] = f_.twx[1];
+    f_.twy[0] = f_.twy[1];
     NS_TRY(dalloc(&red_, B * kRedBlocks));
     NS_TRY(dalloc(&active_, B));
     NS_TRY(dalloc(&ptr_in_, B));
@@ -857,7 +918,6 @@ template <class T> int StepperImpl<T>::init() {
     f_.W = W; f_.P = P; f_.cS = cS; f_.cG = cG;
     f_.X1 = X1; f_.X2 = X2; f_.Wh = Wh; f_.Nh = Nh;
     f_.tA = tA; f_.tB = tB; f_.tP = tP;
-    f_.twx = twx; f_.twy = twy;
     f_.Y = nullptr;
     f_.Ub = f_.Vb = f_.DxOb = f_.DyOb = nullptr;
     f_.active = active_;
