@@ -99,8 +99,11 @@ template <class T> struct SpecOp {
 
 // ------------------------------------------------------------ point values
 
+// Value of row j at column i for the forward row pass.  PEN modes return the
+// new vorticity (and the new SFD filter value in *y_new) without storing
+// them, so that a thread can issue all of its loads before its first store.
 template <class T, int MODE>
-__device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sfd) {
+__device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sfd, T* y_new) {
     const int nx = f.nx, ny = f.ny;
     const int ip = (i + 1) & (nx - 1), im = (i - 1) & (nx - 1);
     const int jp = (j + 1) & (ny - 1), jm = (j - 1) & (ny - 1);
@@ -149,10 +152,9 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
         if (sfd) {
             const T y = f.Y[c];
             const T d = w - y;
-            f.Y[c] = y + f.sfd_k2 * d;
+            *y_new = y + f.sfd_k2 * d;
             w = w - f.sfd_k1 * d;
         }
-        f.W[c] = w;
         return w;
     }
 }
@@ -173,19 +175,41 @@ __global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool
     C* s = reinterpret_cast<C*>(smem_raw);
     const int nx = f.nx, S = seq_stride(nx, RP, (int)sizeof(C) / 4);
     const int pair0 = blockIdx.x * RP;
-    for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
+    constexpr int E = 1 << LE;   // RP*nx values over RP*nx/E threads: exactly E each
+    constexpr bool PEN = (MODE == FWD_PEN_NL || MODE == FWD_PEN_LIN);
+    T va[E], vb[E], ya[PEN ? E : 1], yb[PEN ? E : 1];
+#pragma unroll
+    for (int it = 0; it < E; ++it) {
+        const int e = threadIdx.x + it * blockDim.x;
         const int p = e >> f.logx, i = e & (nx - 1);
         const int j0 = 2 * (pair0 + p);
-        const T a = row_value<T, MODE>(f, i, j0, sfd);
-        const T b = row_value<T, MODE>(f, i, j0 + 1, sfd);
-        s[p * S + sw<T>(i)] = mk<T>(a, b);
+        va[it] = row_value<T, MODE>(f, i, j0, sfd, &ya[PEN ? it : 0]);
+        vb[it] = row_value<T, MODE>(f, i, j0 + 1, sfd, &yb[PEN ? it : 0]);
+    }
+#pragma unroll
+    for (int it = 0; it < E; ++it) {
+        const int e = threadIdx.x + it * blockDim.x;
+        const int p = e >> f.logx, i = e & (nx - 1);
+        const int j0 = 2 * (pair0 + p);
+        if (PEN) {
+            const size_t c = (size_t)j0 * nx + i;
+            f.W[c] = va[it];
+            f.W[c + nx] = vb[it];
+            if (sfd) {
+                f.Y[c] = ya[PEN ? it : 0];
+                f.Y[c + nx] = yb[PEN ? it : 0];
+            }
+        }
+        s[p * S + sw<T>(i)] = mk<T>(va[it], vb[it]);
     }
     if (!do_fft) return;
     __syncthreads();
     fft_smem<false, T, LE>(s, f.logx, S, RP, f.twx[LE]);
     // split Z = FFT(a + i b) into the half-spectra of a and b
     const int nh = nx >> 1;
-    for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < E / 2; ++it) {
+        const int e = threadIdx.x + it * blockDim.x;
         const int p = e & (RP - 1), k = e >> logRP;
         const int j0 = 2 * (pair0 + p);
         const C* z = s + p * S;
@@ -219,17 +243,25 @@ __global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP, bool
     C* s = reinterpret_cast<C*>(smem_raw);
     const int nx = f.nx, ny = f.ny, nh = nx >> 1, S = seq_stride(nx, RP, (int)sizeof(C) / 4);
     const int pair0 = blockIdx.x * RP;
-    for (int e = threadIdx.x; e < (RP * nh); e += blockDim.x) {
+    constexpr int E = 1 << LE;   // RP*nh spectra over RP*nx/E threads: E/2 each
+    C Av[E / 2], Bv[E / 2];
+#pragma unroll
+    for (int it = 0; it < E / 2; ++it) {
+        const int e = threadIdx.x + it * blockDim.x;
         const int p = e & (RP - 1), k = e >> logRP;
-        const int pr = pair0 + p;
-        const int ra = same ? 2 * pr : pr;
-        C A, B;
+        const int ra = same ? 2 * (pair0 + p) : pair0 + p;
         if (same) {
-            PairIO<T>::load(XA + (size_t)k * ny + ra, A, B);       // rows 2pr, 2pr+1 are adjacent
+            PairIO<T>::load(XA + (size_t)k * ny + ra, Av[it], Bv[it]);   // rows 2pr, 2pr+1 are adjacent
         } else {
-            A = XA[(size_t)k * ny + ra];
-            B = XB[(size_t)k * ny + ra];
+            Av[it] = XA[(size_t)k * ny + ra];
+            Bv[it] = XB[(size_t)k * ny + ra];
         }
+    }
+#pragma unroll
+    for (int it = 0; it < E / 2; ++it) {
+        const int e = threadIdx.x + it * blockDim.x;
+        const int p = e & (RP - 1), k = e >> logRP;
+        const C A = Av[it], B = Bv[it];
         C* z = s + p * S;
         if (k == 0) {
             z[0] = mk<T>(A.x, B.x);
@@ -241,7 +273,9 @@ __global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP, bool
     }
     __syncthreads();
     fft_smem<true, T, LE>(s, f.logx, S, RP, f.twx[LE]);
-    for (int e = threadIdx.x; e < (RP << f.logx); e += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < E; ++it) {
+        const int e = threadIdx.x + it * blockDim.x;
         const int p = e >> f.logx, i = e & (nx - 1);
         const int pr = pair0 + p;
         const int ra = same ? 2 * pr : pr;
@@ -273,9 +307,16 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     const int ny = f.ny, logy = f.logy;
     const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
     const int c0 = blockIdx.x * CP;
-    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
-        const int c = e >> logy, j = e & (ny - 1);
-        s[c * S + sw<T>(j)] = f.X1[(size_t)(c0 + c) * ny + j];
+    constexpr int E = 1 << LE;   // CP*ny values over CP*ny/E threads: E each
+    {
+        C v[E];
+#pragma unroll
+        for (int it = 0; it < E; ++it) v[it] = f.X1[(size_t)c0 * ny + threadIdx.x + it * blockDim.x];
+#pragma unroll
+        for (int it = 0; it < E; ++it) {
+            const int e = threadIdx.x + it * blockDim.x;
+            s[(e >> logy) * S + sw<T>(e & (ny - 1))] = v[it];
+        }
     }
     __syncthreads();
     fft_smem<false, T, LE>(s, logy, S, CP, f.twy[LE]);
@@ -321,13 +362,25 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
     C* s2 = s1 + (size_t)CP * S;   // omega^ in, psi*^ out
     C* s3 = s2 + (size_t)CP * S;   // N^{n-1} in
     const int c0i = blockIdx.x * CP;
+    constexpr int E = 1 << LE;   // CP*ny values over CP*ny/E threads: E each
     // all three input columns are read at once (one wait for the whole block)
-    for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
-        const int c = e >> logy, j = e & (ny - 1);
-        const size_t g = (size_t)(c0i + c) * ny + j;
-        s1[c * S + sw<T>(j)] = f.X1[g];
-        s2[c * S + sw<T>(j)] = f.Wh[g];
-        if (!first) s3[c * S + sw<T>(j)] = f.Nh[g];
+    {
+        C a[E], b[E], c3[E];
+#pragma unroll
+        for (int it = 0; it < E; ++it) {
+            const size_t g = (size_t)c0i * ny + threadIdx.x + it * blockDim.x;
+            a[it] = f.X1[g];
+            b[it] = f.Wh[g];
+            if (!first) c3[it] = f.Nh[g];
+        }
+#pragma unroll
+        for (int it = 0; it < E; ++it) {
+            const int e = threadIdx.x + it * blockDim.x;
+            const int o = (e >> logy) * S + sw<T>(e & (ny - 1));
+            s1[o] = a[it];
+            s2[o] = b[it];
+            if (!first) s3[o] = c3[it];
+        }
     }
     __syncthreads();
     fft_smem<false, T, LE>(s1, logy, S, CP, f.twy[LE]);
