@@ -133,6 +133,30 @@ int sfd_baseflow(nsstab_stepper* st, double* omega, double chi, double Delta,
                  double tol, long max_steps, int check_every,
                  double* residual, long* steps);
 
+/* Steady base flow by Newton-Krylov (Sec. 3.1.2, Eq. 43): iterate
+ *   q <- q - (I - M)^{-1} (q - Phi_T(q)),
+ * Phi_T = T/dt nonlinear steps (AB1 start), M = exp(T A) about the current
+ * iterate, the linear system solved by GMRES(gmres_m) with CGS2 to the
+ * relative residual 1e-3 (at most 2 restarts), until the base-flow residual
+ * r(q) of stepper_residual is <= tol or max_newton Newton steps were made.
+ * Unlike SFD it also converges to unstable steady states with real
+ * (non-oscillating) unstable eigenvalues.  omega: device [ny][nx], in:
+ * initial guess, out: last iterate.  *residual (r of the last iterate),
+ * *newton_iters, *matvecs (products with M): host.  Allocates
+ * n (gmres_m + 5) doubles during the call.  Single steppers only.  Returns
+ * NSSTAB_OK, NSSTAB_NOT_CONVERGED or NSSTAB_DIVERGED.  Synchronous. */
+int newton_krylov_fixedpoint(nsstab_stepper* st, double* omega, double T, int gmres_m,
+                             double tol, int max_newton, double* residual,
+                             int* newton_iters, int* matvecs);
+
+/* The same with the Krylov products taken from lin_st (same grid and dt;
+ * NULL = st), e.g. an FP32 stepper while st (FP64) evaluates Phi_T and the
+ * residual, and with the GMRES relative tolerance and restart count given. */
+int newton_krylov_fixedpoint_ex(nsstab_stepper* st, nsstab_stepper* lin_st, double* omega,
+                                double T, int gmres_m, double gmres_rtol, int gmres_restarts,
+                                double tol, int max_newton, double* residual,
+                                int* newton_iters, int* matvecs);
+
 /* Leading eigenvalues of M = exp(T A) about base_omega (Sec. 3.2).
  * max_restarts == 0: one m-step Arnoldi factorisation (Algorithm 1) with
  * CGS2.  max_restarts > 0: Krylov-Schur (Sec. 3.2.2) of order m, restarted

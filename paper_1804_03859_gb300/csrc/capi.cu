@@ -9,6 +9,7 @@
 
 #include "arnoldi.h"
 #include "dense_eig.h"
+#include "newton.h"
 #include "stepper.cuh"
 
 struct nsstab_stepper {
@@ -246,6 +247,34 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
         if (status == NSSTAB_OK && o.status != NSSTAB_OK) status = o.status;
     }
     return status;
+}
+
+int newton_krylov_fixedpoint_ex(nsstab_stepper* st, nsstab_stepper* lin_st, double* omega, double T, int gmres_m,
+                                double gmres_rtol, int gmres_restarts, double tol, int max_newton, double* residual,
+                                int* newton_iters, int* matvecs) {
+    if (!st || !omega || !residual || !newton_iters || !matvecs)
+        return bad_arg("newton_krylov_fixedpoint: null argument");
+    nsstab_stepper* lin = lin_st ? lin_st : st;
+    if (st->impl->members() != 1 || lin->impl->members() != 1)
+        return bad_arg("newton_krylov_fixedpoint: single steppers only");
+    if (lin->cfg.nx != st->cfg.nx || lin->cfg.ny != st->cfg.ny || lin->cfg.dt != st->cfg.dt)
+        return bad_arg("newton_krylov_fixedpoint: lin_st must have the grid and dt of st");
+    if (gmres_m < 1 || gmres_m > 1024 || gmres_restarts < 0 || !(gmres_rtol > 0) || !(tol >= 0) || max_newton < 0)
+        return bad_arg("newton_krylov_fixedpoint: need 1 <= gmres_m <= 1024, gmres_restarts >= 0, gmres_rtol > 0, "
+                       "tol >= 0, max_newton >= 0");
+    int nsteps = 0;
+    NS_TRY(steps_for(st->cfg, T, &nsteps));
+    const long n = (long)st->cfg.nx * st->cfg.ny;
+    const int rc = newton_run(st->impl, lin->impl, st->stream, n, omega, nsteps, gmres_m, gmres_rtol, gmres_restarts,
+                              tol, max_newton, residual, newton_iters, matvecs);
+    lin->have_base = true;
+    return rc;
+}
+
+int newton_krylov_fixedpoint(nsstab_stepper* st, double* omega, double T, int gmres_m, double tol, int max_newton,
+                             double* residual, int* newton_iters, int* matvecs) {
+    return newton_krylov_fixedpoint_ex(st, nullptr, omega, T, gmres_m, 1e-3, 2, tol, max_newton, residual,
+                                       newton_iters, matvecs);
 }
 
 int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, double* kernel_ms) {

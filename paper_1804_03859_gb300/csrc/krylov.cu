@@ -72,6 +72,12 @@ __global__ void k_gs_update(double* __restrict__ w, const double* __restrict__ V
     }
 }
 
+// dst = a x + b y (dst may alias x or y)
+__global__ void k_axpby(double* dst, double a, const double* x, double b, const double* y, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        dst[i] = a * x[i] + b * y[i];
+}
+
 __global__ void k_scale(double* __restrict__ dst, const double* __restrict__ src, long n, double s) {
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
         dst[i] = src[i] * s;
@@ -333,6 +339,12 @@ int vec_norm(const double* x, long n, double* out, GsWork& ws, cudaStream_t stre
     NS_CUDA(cudaMemcpyAsync(ws.hhost, b2, sizeof(double), cudaMemcpyDeviceToHost, stream));
     NS_CUDA(cudaStreamSynchronize(stream));
     *out = std::sqrt(ws.hhost[0]);
+    return NSSTAB_OK;
+}
+
+int vec_axpby(double* dst, double a, const double* x, double b, const double* y, long n, cudaStream_t stream) {
+    k_axpby<<<kGsBlocks, kGsThreads, 0, stream>>>(dst, a, x, b, y, n);
+    NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
 

@@ -75,6 +75,7 @@ int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j,
 int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream);
 int vec_norm(const double* x, long n, double* out, GsWork& ws, cudaStream_t stream);
 int vec_scale(double* dst, const double* src, long n, double s, cudaStream_t stream);
+int vec_axpby(double* dst, double a, const double* x, double b, const double* y, long n, cudaStream_t stream);
 // out[:, c] = sum_k V[:, k] C[k, c] for c < p (C: device, column-major
 // m x p); out must not alias V.
 int basis_combine(const double* V, long ldv, long n, int m, const double* C_dev, int p,

@@ -57,6 +57,11 @@ SIGNATURES = [
     ("stepper_residual", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, _dp]),
     ("sfd_baseflow", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_long, ctypes.c_int, _dp, _lp]),
+    ("newton_krylov_fixedpoint", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                                ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]),
+    ("newton_krylov_fixedpoint_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                                   ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]),
     ("arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                     ctypes.c_void_p, _ip, _ip, _ip]),
@@ -322,6 +327,19 @@ class Stepper:
                                            ctypes.byref(steps)),
                     "sfd_baseflow", allow_soft=True)
         return rc, (float(r[0]) if self.members == 1 else r), steps.value
+
+    def newton_krylov_fixedpoint(self, omega, T: float, gmres_m: int, tol: float, max_newton: int,
+                                 lin=None, gmres_rtol: float = 1e-3, gmres_restarts: int = 2):
+        """Newton-Krylov base flow; lin: optional second Stepper for the Jacobian products."""
+        r = ctypes.c_double()
+        it, mv = ctypes.c_int(), ctypes.c_int()
+        rc = _check(self._lib.newton_krylov_fixedpoint_ex(self._h, lin._h if lin is not None else None,
+                                                          self._p(omega, "omega"), float(T), int(gmres_m),
+                                                          float(gmres_rtol), int(gmres_restarts), float(tol),
+                                                          int(max_newton), ctypes.byref(r), ctypes.byref(it),
+                                                          ctypes.byref(mv)),
+                    "newton_krylov_fixedpoint", allow_soft=True)
+        return rc, r.value, it.value, mv.value
 
     def batch_arnoldi_eigs(self, bases, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
                            eigvecs=None) -> list:
