@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--no-eigs", action="store_true", help="skip the time-to-eigenvalues legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch plans (skip the autotuner)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (16 Reynolds numbers) leg")
     return ap.parse_args()
 
 
@@ -126,6 +127,27 @@ def peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+# ------------------------------------------------------------- multi-rank
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x itself
+    when no group is initialised): the job's time is its slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, pts_per_step: int, elapsed_max: float) -> float:
+    """Whole-job grid-point steps per second: every rank runs its own replica
+    of the workload (weak scaling), the job takes the slowest rank's time."""
+    return world * steps * pts_per_step / elapsed_max
 
 
 # ---------------------------------------------------------------- clocks
@@ -298,19 +320,16 @@ def run_native(args, rank: int, world: int):
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
-            t = torch.tensor([total], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
-        return total / 1e3
+        return max_over_ranks(total, dev) / 1e3
 
     st64 = make(64)
     with ClockSampler(local) as clk:
         el64 = timed(st64, args.steps, args.warmup)
-    value = world * args.steps * pts_per_step / el64
+    value = job_value(world, args.steps, pts_per_step, el64)
 
     st32 = make(32)
     el32 = timed(st32, args.steps, args.warmup)
-    value32 = world * args.steps * pts_per_step / el32
+    value32 = job_value(world, args.steps, pts_per_step, el32)
 
     # end to end through host buffers: H2D of v, M v + CGS2, D2H of w
     host_v = torch.from_numpy(inputs.gaussian_field(NY, NX, seed=2)).pin_memory()
@@ -368,6 +387,49 @@ def run_native(args, rank: int, world: int):
                 d["rel_err_vs_fp64"] = errs
             eigs[f"fp{prec}"] = d
 
+    # batched: 16 Reynolds numbers in 40..100 (one base flow each) stepped in
+    # one launch per kernel, FP32 stepper, and their 16 eigenproblems solved
+    # together by the lockstep batched Krylov-Schur driver
+    batched = None
+    if not args.no_batch:
+        nb = 16
+        Res = [float(x) for x in np.linspace(40.0, 100.0, nb)]
+        stb = nsstab.Stepper(nx=NX, ny=NY, dt=DT, Re=Res, precision=32)
+        if not args.no_tune:
+            stb.stepper_autotune(reps=3)
+        bases = torch.from_numpy(np.stack([inputs.wake_like_field(NY, NX, seed=k) for k in range(nb)])).to(dev)
+        vb = torch.from_numpy(np.stack([inputs.gaussian_field(NY, NX, seed=100 + k) for k in range(nb)])).to(dev)
+        wb = torch.empty_like(vb)
+        stb.stepper_set_base(bases)
+        for _ in range(args.warmup):
+            stb.apply_expTL(None, vb, wb, T_SAMPLE)
+        torch.cuda.synchronize()
+        tb = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            stb.apply_expTL(None, vb, wb, T_SAMPLE)
+            e1.record()
+            e1.synchronize()
+            tb += e0.elapsed_time(e1) / 1e3
+        tb = max_over_ranks(tb, dev)
+        batched = {"members": nb, "Re": [Res[0], Res[-1]], "precision": "f32",
+                   "value": job_value(world, args.steps, nb * pts_per_step, tb), "unit": UNIT,
+                   "ms_per_step": 1e3 * tb / args.steps, "plans": stb.plans()}
+        if not args.no_eigs:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rs = stb.batch_arnoldi_eigs(None, vb, m=KRYLOV_M, nev=NEV, tol=1e-5, T=T_SAMPLE, max_restarts=4)
+            elb = time.perf_counter() - t0
+            batched["time_to_eigs"] = {
+                "seconds": elb, "members_converged": int(sum(r.n_conv >= len(r.mu) for r in rs)),
+                "n_matvec_total": int(sum(r.n_matvec for r in rs)), "tol": 1e-5,
+                "sequential_estimate_seconds": (eigs or {}).get("fp32", {}).get("seconds", float("nan")) * nb,
+                "sequential_estimate": "16 x the measured single-solve FP32 time above (same m, nev, tol)"}
+        del stb
+
     if rank != 0:
         return
     clocks = clk.summary()
@@ -398,6 +460,7 @@ def run_native(args, rank: int, world: int):
         "step_flops_fp64": step_flops,
         "step_tflops_fp64": step_flops * nsteps / (el64 / args.steps) / 1e12,
         "time_to_eigs": eigs,
+        "batched": batched,
     }
     print(json.dumps(out))
 
