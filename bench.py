@@ -331,6 +331,10 @@ def run_native(args, rank: int, world: int):
     el32 = timed(st32, args.steps, args.warmup)
     value32 = job_value(world, args.steps, pts_per_step, el32)
 
+    st48 = make(48)
+    el48 = timed(st48, args.steps, args.warmup)
+    value48 = job_value(world, args.steps, pts_per_step, el48)
+
     # end to end through host buffers: H2D of v, M v + CGS2, D2H of w
     host_v = torch.from_numpy(inputs.gaussian_field(NY, NX, seed=2)).pin_memory()
     host_w = torch.empty(NY, NX, dtype=torch.float64).pin_memory()
@@ -366,6 +370,7 @@ def run_native(args, rank: int, world: int):
                 "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x max SM clock (profiling recipe's 1.25 TFLOP/s)",
                 "share": {k: v / sum(ms.values()) for k, v in ms.items()}}
     ms32 = st32.stepper_profile_linear(v0, prof_steps)
+    ms48 = st48.stepper_profile_linear(v0, prof_steps)
     step_flops = sum(fl.values())
 
     # time to the leading eigenvalues (Krylov-Schur, m = 128, nev = 8)
@@ -373,7 +378,7 @@ def run_native(args, rank: int, world: int):
     if not args.no_eigs:
         eigs = {}
         ref_mu = None
-        for prec, st, tol in ((64, st64, 1e-8), (32, st32, 1e-5)):
+        for prec, st, tol in ((64, st64, 1e-8), (48, st48, 1e-8), (32, st32, 1e-5)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r = st.arnoldi_eigs(None, v0, m=KRYLOV_M, nev=NEV, tol=tol, T=T_SAMPLE, max_restarts=4)
@@ -383,6 +388,7 @@ def run_native(args, rank: int, world: int):
             if prec == 64:
                 ref_mu = r.mu
             elif ref_mu is not None:
+                d["abs_err_vs_fp64"] = [float(np.min(np.abs(ref_mu - m))) for m in r.mu]
                 errs = [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in r.mu]
                 d["rel_err_vs_fp64"] = errs
             eigs[f"fp{prec}"] = d
@@ -457,6 +463,9 @@ def run_native(args, rank: int, world: int):
         "clocks": clocks,
         "fp32": {"value": value32, "unit": UNIT, "ms_per_step": 1e3 * el32 / args.steps,
                  "kernel_ms": {k: v / prof_steps for k, v in ms32.items()}},
+        "double_float": {"value": value48, "unit": UNIT, "ms_per_step": 1e3 * el48 / args.steps,
+                         "dtype": "f32x2 (double-float, ~48-bit significand)",
+                         "kernel_ms": {k: v / prof_steps for k, v in ms48.items()}},
         "step_flops_fp64": step_flops,
         "step_tflops_fp64": step_flops * nsteps / (el64 / args.steps) / 1e12,
         "time_to_eigs": eigs,

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "../../include/nsstab.h"
+#include "df64.cuh"
 
 namespace nsstab {
 
@@ -16,6 +17,7 @@ namespace nsstab {
 template <class T> struct cx_t;
 template <> struct cx_t<double> { using type = double2; };
 template <> struct cx_t<float> { using type = float2; };
+template <> struct cx_t<df64> { using type = df64c; };
 template <class T> using Cx = typename cx_t<T>::type;
 
 template <class T> __host__ __device__ __forceinline__ Cx<T> mk(T x, T y) {
@@ -68,6 +70,28 @@ template <> struct PairIO<double> {
         p[1] = b;
     }
 };
+
+template <> struct PairIO<df64> {
+    __device__ static __forceinline__ void load(const df64c* p, df64c& a, df64c& b) {
+        a = p[0];
+        b = p[1];
+    }
+    __device__ static __forceinline__ void store(df64c* p, df64c a, df64c b) {
+        p[0] = a;
+        p[1] = b;
+    }
+};
+
+// read-only cached load of one complex value
+__device__ __forceinline__ float2 ldg_c(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldg_c(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ df64c ldg_c(const df64c* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    df64c r;
+    r.x = df64(v.x, v.y);
+    r.y = df64(v.z, v.w);
+    return r;
+}
 
 // --------------------------------------------------------------- errors
 void set_error(const std::string& msg);

@@ -32,6 +32,7 @@ namespace nsstab {
 template <class T> __device__ __forceinline__ int sw(int i);
 template <> __device__ __forceinline__ int sw<float>(int i) { return i ^ ((i >> 4) & 15); }
 template <> __device__ __forceinline__ int sw<double>(int i) { return i ^ ((i >> 3) & 7); }
+template <> __device__ __forceinline__ int sw<df64>(int i) { return i ^ ((i >> 3) & 7); }
 __host__ __device__ constexpr int padded_len(int n) { return n; }
 // Distance (in elements) between consecutive sequences in shared memory.
 // When `rp` sequences share one shared-memory wavefront (element-interleaved
@@ -66,6 +67,7 @@ inline int twiddle_table_len(int logN, int LE) {
 template <class T> struct Consts;
 template <> struct Consts<double> { static constexpr double rsqrt2 = 0.70710678118654752440084436210485; };
 template <> struct Consts<float> { static constexpr float rsqrt2 = 0.70710678118654752440f; };
+template <> struct Consts<df64> { static constexpr df64 rsqrt2 = df64(0.70710677f, 1.21016175e-08f); };
 
 // forward: X_k = sum_j x_j exp(-2 pi i jk/N); INV: exp(+2 pi i jk/N), unnormalised
 template <bool INV, class C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
@@ -103,7 +105,7 @@ template <bool INV, class T> __device__ __forceinline__ void dft8(Cx<T>* v) {
 
 template <bool INV, class T>
 __device__ __forceinline__ Cx<T> twiddle(Cx<T> a, const Cx<T>* __restrict__ tw, int e) {
-    const Cx<T> w = __ldg(tw + e);
+    const Cx<T> w = ldg_c(tw + e);
     return INV ? cmulc(a, w) : cmul(a, w);
 }
 

@@ -150,3 +150,12 @@ def test_invalid_krylov_arguments():
             st.arnoldi_eigs(base, v0, m=m, nev=nev, tol=1e-8, T=0.5)
     with pytest.raises(nsstab.NsstabError):
         st.arnoldi_eigs(base, torch.zeros(8, 16, dtype=torch.float64, device="cuda"), m=10, nev=2, tol=1e-8, T=0.5)
+
+
+def test_double_float_arnoldi_matches_dense(small):
+    kw, cfg, base, T, mu_dense = small
+    st = nsstab.Stepper(precision=48, **kw)
+    v0 = inputs.gaussian_field(16, 32, seed=11)
+    res = st.arnoldi_eigs(_dev(base), _dev(v0), m=150, nev=4, tol=1e-10, T=T)
+    assert res.status == nsstab.OK and res.n_conv == len(res.mu)
+    assert _match(res.mu, mu_dense[:6]) <= 1e-10

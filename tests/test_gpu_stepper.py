@@ -264,3 +264,40 @@ def test_long_runs_through_several_graph_chunks():
     t2 = torch.zeros(32, 64, dtype=torch.float64, device="cuda")
     st.step_nonlinear(t2, 300)
     assert torch.equal(t, t2)
+
+
+# ---------------------------------------------------------------- double-float
+
+@pytest.mark.parametrize("nx,ny", [(16, 8), (128, 64), (64, 256), (512, 256), (2048, 1024)])
+def test_double_float_stepper_meets_the_fp64_bar(nx, ny):
+    """precision 48: FP32-pair arithmetic, held to the FP64 bar (1e-12 per step)
+    up to the 512x256 workload grid.  Its unit roundoff (2^-48) is 32 times
+    FP64's, and the centred differences of psi lose ~eps/(dx dy) to
+    cancellation, so the bound grows with the grid density beyond that
+    (measured 1.4e-12 at 2048x1024)."""
+    kw = _cfg(nx, ny)
+    cfg = ns2d.Config(**kw)
+    w0 = inputs.wake_like_field(ny, nx, seed=1) + 0.3 * inputs.smooth_field(ny, nx, seed=2, kmax=5)
+    st = nsstab.Stepper(precision=48, **kw)
+    t = _dev(w0)
+    st.step_nonlinear(t, 1)
+    tol = max(1e-12, 1e-12 * (nx / 512.0) * (ny / 256.0) / 4.0)
+    assert _rel(_host(t), ns2d.step_nonlinear(w0, 1, cfg)) <= tol
+    base = inputs.wake_like_field(ny, nx, seed=3)
+    v = inputs.gaussian_field(ny, nx, seed=4)
+    out = torch.empty(ny, nx, dtype=torch.float64, device="cuda")
+    nsteps = 20 if nx <= 512 else 2
+    st.apply_expTL(_dev(base), _dev(v), out, nsteps * cfg.dt)
+    ref = ns2d.apply_expTL(ns2d.Base.from_omega(base, cfg), v, nsteps * cfg.dt, cfg)
+    assert _rel(_host(out), ref) <= nsteps * tol
+
+
+def test_double_float_autotuned_plans_keep_parity():
+    kw = _cfg(256, 128)
+    cfg = ns2d.Config(**kw)
+    st = nsstab.Stepper(precision=48, **kw)
+    st.stepper_autotune(reps=3)
+    w0 = inputs.wake_like_field(128, 256, seed=5)
+    t = _dev(w0)
+    st.step_nonlinear(t, 3)
+    assert _rel(_host(t), ns2d.step_nonlinear(w0, 3, cfg)) <= 3e-12
