@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch plans (skip the autotuner)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (16 Reynolds numbers) leg")
+    ap.add_argument("--profile-case", default=None, metavar="NXxNY",
+                    help="only run --steps linearised steps of one stepper on this grid (for ncu captures)")
+    ap.add_argument("--precision", type=int, default=64, help="stepper precision of --profile-case (64, 48, 32)")
+    ap.add_argument("--members", type=int, default=1, help="batch members of --profile-case")
     return ap.parse_args()
 
 
@@ -104,7 +108,7 @@ def kernel_flops(nx: int, ny: int) -> dict:
 
 def src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("stepper.cu", "fft.cuh", "common.cuh", "stepper.cuh"):
+    for f in ("stepper_impl.cuh", "fft.cuh", "common.cuh", "stepper.cuh", "df64.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1804_03859_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -474,8 +478,35 @@ def run_native(args, rank: int, world: int):
     print(json.dumps(out))
 
 
+def run_profile_case(args):
+    """A small fixed workload for profilers: one stepper (or a batch), a
+    wake-like base flow, --steps linearised steps.  Prints one line."""
+    import torch
+
+    from paper_1804_03859_gb300 import build, inputs, nsstab
+
+    build.build()
+    nx, ny = (int(x) for x in args.profile_case.lower().split("x"))
+    dt = 0.01 * 128 / nx
+    B = args.members
+    kw = dict(nx=nx, ny=ny, dt=dt, precision=args.precision)
+    st = nsstab.Stepper(Re=list(np.linspace(40.0, 100.0, B)), **kw) if B > 1 else nsstab.Stepper(Re=RE, **kw)
+    shape = (B, ny, nx) if B > 1 else (ny, nx)
+    base = torch.from_numpy(np.stack([inputs.wake_like_field(ny, nx, seed=k) for k in range(B)]).reshape(shape)).cuda()
+    v = torch.from_numpy(np.stack([inputs.gaussian_field(ny, nx, seed=10 + k) for k in range(B)]).reshape(shape)).cuda()
+    w = torch.empty_like(v)
+    st.stepper_set_base(base)
+    st.apply_expTL(None, v, w, args.steps * dt)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "precision": args.precision, "members": B,
+                      "steps": args.steps, "max_abs": float(w.abs().max())}))
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
