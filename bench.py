@@ -47,6 +47,7 @@ T_SAMPLE = 0.5
 KRYLOV_M = 128
 BASIS_J = KRYLOV_M // 2       # basis size the timed CGS2 runs against
 NEV = 8
+TOL32 = 1e-6                  # Ritz residual tolerance of the FP32 eigen-solves (1e-5 eigenvalue target)
 WORKLOAD = "cylinder wake 512x256, Re 60, Krylov step: M v (T=0.5, 200 linearised steps) + CGS2 vs 64 vectors"
 L2_FLUSH_BYTES = 512 << 20
 N_SMS = 152
@@ -63,6 +64,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch plans (skip the autotuner)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (16 Reynolds numbers) leg")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg (24 solves on mixed grids)")
+    ap.add_argument("--serve-grids", default="256x128,512x256,1024x512",
+                    help="grids the serving leg draws its solves from")
     ap.add_argument("--profile-case", default=None, metavar="NXxNY",
                     help="only run --steps linearised steps of one stepper on this grid (for ncu captures)")
     ap.add_argument("--precision", type=int, default=64, help="stepper precision of --profile-case (64, 48, 32)")
@@ -382,7 +386,7 @@ def run_native(args, rank: int, world: int):
     if not args.no_eigs:
         eigs = {}
         ref_mu = None
-        for prec, st, tol in ((64, st64, 1e-8), (48, st48, 1e-8), (32, st32, 1e-5)):
+        for prec, st, tol in ((64, st64, 1e-8), (48, st48, 1e-8), (32, st32, TOL32)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r = st.arnoldi_eigs(None, v0, m=KRYLOV_M, nev=NEV, tol=tol, T=T_SAMPLE, max_restarts=4)
@@ -431,14 +435,21 @@ def run_native(args, rank: int, world: int):
         if not args.no_eigs:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            rs = stb.batch_arnoldi_eigs(None, vb, m=KRYLOV_M, nev=NEV, tol=1e-5, T=T_SAMPLE, max_restarts=4)
+            rs = stb.batch_arnoldi_eigs(None, vb, m=KRYLOV_M, nev=NEV, tol=TOL32, T=T_SAMPLE, max_restarts=4)
             elb = time.perf_counter() - t0
             batched["time_to_eigs"] = {
                 "seconds": elb, "members_converged": int(sum(r.n_conv >= len(r.mu) for r in rs)),
-                "n_matvec_total": int(sum(r.n_matvec for r in rs)), "tol": 1e-5,
+                "n_matvec_total": int(sum(r.n_matvec for r in rs)), "tol": TOL32,
                 "sequential_estimate_seconds": (eigs or {}).get("fp32", {}).get("seconds", float("nan")) * nb,
                 "sequential_estimate": "16 x the measured single-solve FP32 time above (same m, nev, tol)"}
         del stb
+
+    # serving: 24 independent eigen-solves with grids, Reynolds numbers and
+    # cylinder diameters drawn at random, run by serve_eigs (grouped by grid
+    # into batched FP32 steppers, groups concurrent on their own streams)
+    serving = None
+    if not args.no_serve and not args.no_eigs:
+        serving = serve_leg(args, dev)
 
     if rank != 0:
         return
@@ -474,8 +485,48 @@ def run_native(args, rank: int, world: int):
         "step_tflops_fp64": step_flops * nsteps / (el64 / args.steps) / 1e12,
         "time_to_eigs": eigs,
         "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(out))
+
+
+SERVE_JOBS = 24
+SERVE_M, SERVE_NEV = 64, 4
+
+
+def serve_leg(args, dev):
+    """Latency and throughput of serve_eigs on a seeded mixed-grid batch."""
+    import torch
+
+    from paper_1804_03859_gb300 import inputs, nsstab
+
+    grids = [tuple(int(x) for x in g.lower().split("x")) for g in args.serve_grids.split(",")]
+    rng = np.random.default_rng(5)
+    jobs = []
+    for i in range(SERVE_JOBS):
+        nx, ny = grids[int(rng.integers(len(grids)))]
+        re, d = float(rng.uniform(40.0, 120.0)), float(rng.uniform(0.8, 1.2))
+        jobs.append(dict(nx=nx, ny=ny, dt=0.01 * 128 / nx, Re=re, cyl_D=d,
+                         base=torch.from_numpy(inputs.wake_like_field(ny, nx, seed=200 + i)).to(dev),
+                         v0=torch.from_numpy(inputs.gaussian_field(ny, nx, seed=300 + i)).to(dev)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, res, ngroups = nsstab.serve_eigs(jobs, m=SERVE_M, nev=SERVE_NEV, tol=TOL32, T=T_SAMPLE, max_restarts=4,
+                                         precision=32)
+    wall = time.perf_counter() - t0
+    lat = np.array([r["latency_s"] for r in res])
+    pts = sum(r["n_matvec"] * j["nx"] * j["ny"] * round(T_SAMPLE / j["dt"]) for r, j in zip(res, jobs))
+    mix = {}
+    for j in jobs:
+        k = f"{j['nx']}x{j['ny']}"
+        mix[k] = mix.get(k, 0) + 1
+    return {"solves": SERVE_JOBS, "grids": mix, "Re": [40.0, 120.0], "cyl_D": [0.8, 1.2], "precision": "f32",
+            "krylov_m": SERVE_M, "nev": SERVE_NEV, "tol": TOL32, "T": T_SAMPLE, "groups": ngroups, "status": rc,
+            "converged": int(sum(r["status"] == nsstab.OK for r in res)),
+            "wall_seconds": wall, "solves_per_s": SERVE_JOBS / wall,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max()), "min": float(lat.min())},
+            "grid_pt_steps_per_s": pts / wall}
 
 
 def run_profile_case(args):

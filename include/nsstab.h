@@ -249,6 +249,70 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
                        double* eig_re, double* eig_im, double* resid, double* eigvecs,
                        int* n_eig, int* n_conv, int* n_matvec);
 
+/* ------------------------------------------------------------------------
+ * Serving batch: many independent eigen-solves on mixed grids.
+ *
+ * The paper analyses one flow at a time (Sec. 3.2); a parameter study or an
+ * analysis service runs many, on grids of different sizes.  serve_eigs takes
+ * a list of solves that may differ in grid, time step, Reynolds number and
+ * cylinder diameter.  Solves that share (nx, ny, dt) are grouped into
+ * batched steppers (one member per solve, as batch_create with per_set = 1),
+ * split further where a group would not fit the memory budget.  The groups
+ * run concurrently, each on its own CUDA stream and host thread, largest
+ * grids first; a group is admitted only while the device memory held by
+ * the running groups (an upper estimate of stepper workspace plus Krylov
+ * basis) stays within mem_budget.  Every solve is the Krylov-Schur
+ * eigen-solve of batch_arnoldi_eigs (same m, nev, tol, max_restarts, T),
+ * so its Ritz values equal those of arnoldi_eigs on a single stepper of
+ * the same configuration, up to rounding.
+ * --------------------------------------------------------------------- */
+
+/* Ritz values kept per solve: nev <= NSSTAB_SERVE_MAX_EIG - 1. */
+#define NSSTAB_SERVE_MAX_EIG 33
+
+typedef struct {
+    int nx, ny;           /* grid: powers of two, as in nsstab_config */
+    double dt;            /* time step; T / dt must be a whole number */
+    double Re, cyl_D;     /* Reynolds number (> 0), cylinder diameter (>= 0) */
+    const double* base;   /* device [ny][nx]: base-flow vorticity (read only) */
+    const double* v0;     /* device [ny][nx]: starting vector, non-zero (read only) */
+} nsstab_eig_job;
+
+typedef struct {
+    int status;           /* NSSTAB_OK, NSSTAB_NOT_CONVERGED, or an error code < 0 */
+    int n_eig, n_conv, n_matvec;
+    int group;            /* index of the batch the solve ran in */
+    double latency_s;     /* seconds from the call's start to the solve's completion */
+    double eig_re[NSSTAB_SERVE_MAX_EIG];   /* Ritz values mu, |mu| descending */
+    double eig_im[NSSTAB_SERVE_MAX_EIG];
+    double resid[NSSTAB_SERVE_MAX_EIG];    /* their residuals */
+} nsstab_eig_result;
+
+/* Run njobs eigen-solves as described above.
+ *   cfg:        shared physical parameters (Lx, Ly, Uinf, cylinder centre,
+ *               eta, mask_cells, sponge, precision); its nx, ny, dt, Re and
+ *               cyl_D are ignored (each job gives its own)
+ *   jobs:       host array of njobs >= 1 solves
+ *   m, nev, tol, max_restarts, T: as arnoldi_eigs, for every solve
+ *   mem_budget: device bytes the running groups may hold; <= 0 takes 80% of
+ *               the device memory free at the call
+ *   max_concurrent: most groups in flight at once (>= 1; <= 0 means 4)
+ *   results:    host array of njobs, written for every job
+ *   ngroups:    host, number of batches formed (may be NULL)
+ * A job whose single-member batch would exceed mem_budget fails with
+ * NSSTAB_ERR_OUT_OF_MEMORY in its result; the others still run.  The jobs'
+ * base and v0 buffers must hold their values when the call is made (its
+ * own streams do not wait on the caller's streams) and stay valid and
+ * unmodified until it returns; the call uses the current device of the
+ * calling thread, synchronises every stream it creates and returns when
+ * all solves are done.  Returns
+ * the first error code (< 0) of any job, else NSSTAB_NOT_CONVERGED if any
+ * solve did not converge, else NSSTAB_OK.  Argument errors (INVALID_ARG)
+ * are reported before any device work.  Synchronous. */
+int serve_eigs(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+               double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
+               nsstab_eig_result* results, int* ngroups);
+
 /* One CGS2 orthogonalisation (Algorithm 1's Gram-Schmidt step applied
  * twice): h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2;
  * beta = ||w||.  V: device, j columns of length n with leading dimension

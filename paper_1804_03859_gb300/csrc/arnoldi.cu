@@ -15,6 +15,7 @@
 // and beta of each member come back (one small D2H copy), and the m x m
 // projected matrices are factorised on the host in FP64 (dense_eig.cpp).
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -85,8 +86,12 @@ struct Member {
 
 }  // namespace
 
-int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* v0, int m, int nev, double tol,
-                      int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs) {
+double steady_seconds() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
+                      double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs) {
     const double delta = 0.05;   // wanted set |mu| >= 1 - delta (Sec. 3.2.2)
     const int nb = st->members();
     outs.resize(nb);
@@ -110,8 +115,7 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
         for (int b = 0; b < nb; ++b) {
             mem[b].V = Vall.p + (size_t)b * n * (m + 1);
             mem[b].B.assign((size_t)ldb * m, 0.0);
-            NS_CUDA(cudaMemcpyAsync(mem[b].V, v0 + (size_t)b * n, n * sizeof(double), cudaMemcpyDeviceToDevice,
-                                    stream));
+            NS_CUDA(cudaMemcpyAsync(mem[b].V, v0[b], n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
             V0[b] = mem[b].V;
             W0[b] = mem[b].V;
         }
@@ -209,6 +213,7 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
             }
             if (M.conv >= M.k || M.restarts >= max_restarts || M.breakdown) {
                 M.done = true;
+                outs[b].done_at = steady_seconds();
                 continue;
             }
             // ---- Krylov-Schur restart: keep the p wanted Ritz values

@@ -195,7 +195,8 @@ int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
     }
     std::vector<ArnoldiOut> outs(1);
     outs[0].eigvecs = eigvecs;
-    const int rc = arnoldi_batch_run(st->impl, st->stream, n, v0, m, nev, tol, max_restarts, nsteps, outs);
+    const double* v0p[1] = {v0};
+    const int rc = arnoldi_batch_run(st->impl, st->stream, n, v0p, m, nev, tol, max_restarts, nsteps, outs);
     if (rc < 0) return rc;
     const ArnoldiOut& out = outs[0];
     for (int s = 0; s < out.n_eig; ++s) {
@@ -231,7 +232,9 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
     std::vector<ArnoldiOut> outs(B);
     if (eigvecs)
         for (int b = 0; b < B; ++b) outs[b].eigvecs = eigvecs + (size_t)b * (nev + 1) * n;
-    const int rc = arnoldi_batch_run(st->impl, st->stream, n, v0, m, nev, tol, max_restarts, nsteps, outs);
+    std::vector<const double*> v0p(B);
+    for (int b = 0; b < B; ++b) v0p[b] = v0 + (size_t)b * n;
+    const int rc = arnoldi_batch_run(st->impl, st->stream, n, v0p.data(), m, nev, tol, max_restarts, nsteps, outs);
     if (rc < 0) return rc;
     int status = rc;
     for (int b = 0; b < B; ++b) {

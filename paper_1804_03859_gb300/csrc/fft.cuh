@@ -19,7 +19,18 @@
 // GB300 the FP64 pipe is the scarce resource, so no sine or cosine is
 // evaluated on the device, and each butterfly's twiddles are one contiguous
 // row so that the loads of a warp are coalesced.
+//
+// FP32 transforms carry every twiddle as hi + lo (lo = the FP32 rounding
+// error of hi) and fold the lo product into the fused multiply-adds before
+// their final rounding; the radix-8 constant 1/sqrt(2) is split the same
+// way.  A twiddle rounded to FP32 makes the transform a fixed, slightly
+// wrong linear map, and a time-stepper applies that same map at every step,
+// so its error adds up linearly over a run (about 1e-5 relative after a few
+// hundred steps, which then bounds the accuracy of the eigenvalues); with
+// the split only the data-dependent rounding of the arithmetic remains.
 #pragma once
+
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -52,7 +63,7 @@ __host__ __device__ inline int seq_stride(int n, int rp, int elem_words) {
 // with Stockham stride Ns and radix R (in the order fft_smem runs them), R
 // rows of Ns entries exp(-2 pi i r k / (Ns R)), r < R, k < Ns.  Consecutive
 // threads of a pass have consecutive k, so the loads of a warp for one r
-// are contiguous.  Length < 2N.
+// are contiguous.  Length < 2N entries (each kTwWidth<T> Cx<T> slots).
 inline int twiddle_table_len(int logN, int LE) {
     int len = 0, nsl = 0, rem = logN;
     while (rem >= LE) {
@@ -64,10 +75,25 @@ inline int twiddle_table_len(int logN, int LE) {
     return len;
 }
 
+// Cx<T> slots per twiddle entry: FP32 tables store hi and lo side by side.
+template <class T> constexpr int kTwWidth = std::is_same<T, float>::value ? 2 : 1;
+
 template <class T> struct Consts;
 template <> struct Consts<double> { static constexpr double rsqrt2 = 0.70710678118654752440084436210485; };
-template <> struct Consts<float> { static constexpr float rsqrt2 = 0.70710678118654752440f; };
+template <> struct Consts<float> {
+    static constexpr float rsqrt2 = 0.70710678118654752440f;
+    static constexpr float rsqrt2_lo = 1.21016175e-08f;   // 1/sqrt(2) - rsqrt2
+};
 template <> struct Consts<df64> { static constexpr df64 rsqrt2 = df64(0.70710677f, 1.21016175e-08f); };
+
+// s / sqrt(2), with the FP32 constant's rounding error compensated
+template <class T> __device__ __forceinline__ T mul_rsqrt2(T s) {
+    if constexpr (std::is_same<T, float>::value) {
+        return __fmaf_rn(s, Consts<float>::rsqrt2, s * Consts<float>::rsqrt2_lo);
+    } else {
+        return s * Consts<T>::rsqrt2;
+    }
+}
 
 // forward: X_k = sum_j x_j exp(-2 pi i jk/N); INV: exp(+2 pi i jk/N), unnormalised
 template <bool INV, class C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
@@ -87,15 +113,14 @@ template <bool INV, class T> __device__ __forceinline__ void dft8(Cx<T>* v) {
     Cx<T> a1 = cadd(v[1], v[5]), b1 = csub(v[1], v[5]);
     Cx<T> a2 = cadd(v[2], v[6]), b2 = csub(v[2], v[6]);
     Cx<T> a3 = cadd(v[3], v[7]), b3 = csub(v[3], v[7]);
-    const T r = Consts<T>::rsqrt2;
     if (!INV) {
-        b1 = mk<T>((b1.x + b1.y) * r, (b1.y - b1.x) * r);     // (1 - i)/sqrt2
-        b2 = cmul_mi(b2);                                    // -i
-        b3 = mk<T>((b3.y - b3.x) * r, -(b3.x + b3.y) * r);    // (-1 - i)/sqrt2
+        b1 = mk<T>(mul_rsqrt2<T>(b1.x + b1.y), mul_rsqrt2<T>(b1.y - b1.x));     // (1 - i)/sqrt2
+        b2 = cmul_mi(b2);                                                      // -i
+        b3 = mk<T>(mul_rsqrt2<T>(b3.y - b3.x), -mul_rsqrt2<T>(b3.x + b3.y));    // (-1 - i)/sqrt2
     } else {
-        b1 = mk<T>((b1.x - b1.y) * r, (b1.x + b1.y) * r);     // (1 + i)/sqrt2
-        b2 = cmul_pi(b2);                                    // +i
-        b3 = mk<T>(-(b3.x + b3.y) * r, (b3.x - b3.y) * r);    // (-1 + i)/sqrt2
+        b1 = mk<T>(mul_rsqrt2<T>(b1.x - b1.y), mul_rsqrt2<T>(b1.x + b1.y));     // (1 + i)/sqrt2
+        b2 = cmul_pi(b2);                                                      // +i
+        b3 = mk<T>(-mul_rsqrt2<T>(b3.x + b3.y), mul_rsqrt2<T>(b3.x - b3.y));    // (-1 + i)/sqrt2
     }
     dft4<INV>(a0, a1, a2, a3);
     dft4<INV>(b0, b1, b2, b3);
@@ -103,10 +128,26 @@ template <bool INV, class T> __device__ __forceinline__ void dft8(Cx<T>* v) {
     v[4] = a2; v[5] = b2; v[6] = a3; v[7] = b3;
 }
 
+// a * w_e (INV: a * conj(w_e)) for twiddle entry e of table tw
 template <bool INV, class T>
 __device__ __forceinline__ Cx<T> twiddle(Cx<T> a, const Cx<T>* __restrict__ tw, int e) {
-    const Cx<T> w = ldg_c(tw + e);
-    return INV ? cmulc(a, w) : cmul(a, w);
+    if constexpr (std::is_same<T, float>::value) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(tw) + e);   // hi (x, y), lo (z, w)
+        float re, im;
+        if (!INV) {
+            const float lr = a.x * q.z - a.y * q.w, li = a.x * q.w + a.y * q.z;
+            re = __fmaf_rn(a.x, q.x, __fmaf_rn(-a.y, q.y, lr));
+            im = __fmaf_rn(a.x, q.y, __fmaf_rn(a.y, q.x, li));
+        } else {
+            const float lr = a.x * q.z + a.y * q.w, li = a.y * q.z - a.x * q.w;
+            re = __fmaf_rn(a.x, q.x, __fmaf_rn(a.y, q.y, lr));
+            im = __fmaf_rn(a.y, q.x, __fmaf_rn(-a.x, q.y, li));
+        }
+        return mk<float>(re, im);
+    } else {
+        const Cx<T> w = ldg_c(tw + e);
+        return INV ? cmulc(a, w) : cmul(a, w);
+    }
 }
 
 template <bool INV, class T, int LR> __device__ __forceinline__ void dft_r(Cx<T>* v) {
@@ -175,7 +216,7 @@ __device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __res
         const Cx<T>* twp = tw;   // start of this pass's rows
         while (rem >= LE) {
             stockham_pass<INV, T, LE, LE>(d, q, lq, logN, nsl, twp, act);
-            twp += (1 << nsl) << LE;
+            twp += kTwWidth<T> * ((1 << nsl) << LE);
             nsl += LE;
             rem -= LE;
         }

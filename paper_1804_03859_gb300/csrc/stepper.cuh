@@ -21,6 +21,8 @@ struct StepperBase {
     virtual int poisson(const double* omega, double* psi) = 0;
     virtual int step_nonlinear(double* omega, int nsteps) = 0;
     virtual int set_base(const double* base_omega) = 0;
+    // base flows by pointer: host array of S device pointers
+    virtual int set_base_ptrs(const double* const* base_omegas) = 0;
     virtual int step_linear(const double* v_in, double* v_out, int nsteps) = 0;
     // per-member device pointers (host arrays of B); a null input pointer
     // leaves that member out of this call

@@ -13,6 +13,27 @@
 //   row_inverse   X1, X2                    -> W = omega*, P = psi*
 //   row_forward   PEN: W, P (+ SFD state Y) -> W = omega^{n+1}, X1 = its x-spectrum
 //
+// FP32 steppers take three measures against error that a time-stepper
+// would otherwise accumulate over hundreds of steps:
+//  * they carry the velocity instead of the streamfunction: the column
+//    passes form the x-spectra of u' = D_y psi and v = -D_x psi by
+//    multiplying psi^ with the centred-difference symbols i sin(k h)/h (the
+//    same discrete operator as the stencil on psi), and the inverse row
+//    passes produce U, V (and W).  The stencil on a rounded psi loses about
+//    log2(|psi| / (h |D psi|)) bits to cancellation (a per-step error near
+//    7e-6 at 512x256); the spectral form keeps the velocity error at the
+//    rounding of the velocity itself;
+//  * the Crank-Nicolson factor A = (1 + nu dt lam/2)/(1 - nu dt lam/2),
+//    within 1e-3 of 1 for the modes that carry the flow, is stored as
+//    A - 1: an FP32 A is a fixed relative error of up to 3e-8 applied at
+//    every step, which grows linearly over a run;
+//  * their transforms split each twiddle into hi + lo (fft.cuh), for the
+//    same reason.
+// Together these take the FP32 propagator of 200 steps from about 1e-5 to
+// about 1e-6 relative to FP64.  The FP64 and double-float steppers keep psi,
+// the stencil and plain tables (their rounding is far below the parity bar),
+// with 1.5x fewer row transforms.
+//
 // Layouts: physical fields [ny][nx] (x fastest); every spectral array is
 // stored column-major [kx][ky] over the nx/2 packed x-wavenumbers, so the
 // column passes read and write contiguous columns.  The x-transform of a
@@ -26,6 +47,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 #include <vector>
 
 #include "fft.cuh"
@@ -35,6 +57,11 @@ namespace nsstab {
 
 enum RowMode { FWD_PLAIN = 0, FWD_RHS_NL = 1, FWD_RHS_LIN = 2, FWD_PEN_NL = 3, FWD_PEN_LIN = 4 };
 
+// The FP32 stepper's accuracy measures (see the file comment): velocities
+// in place of psi, and the Crank-Nicolson factor stored as A - 1.  (Its
+// transforms also split twiddles into hi + lo; see fft.cuh.)
+template <class T> constexpr bool kF32 = std::is_same<T, float>::value;
+
 template <class T> struct Fields {
     int nx, ny, nxh, logx, logy;
     int bper;              // members per parameter set (member m uses set m / bper)
@@ -42,16 +69,20 @@ template <class T> struct Fields {
     const unsigned char* active;   // per-member flag: inactive members skip every kernel
     T idx2, idy2;          // 1/(2 dx), 1/(2 dy)
     T Uinf;
+    T scale;               // 1/(nx ny), the normalisation of the inverse transform
     T sfd_k1, sfd_k2;      // dt*chi_sfd, dt/Delta
     T* W;                  // omega (physical)
     T* P;                  // psi (physical)
+    T* U; T* V;            // u' = D_y psi, v = -D_x psi (physical; kVel steppers)
     T* Y;                  // SFD filtered state
     const T* cS;           // s/(1+s), s = dt (chi/eta + sigma)
     const T* cG;           // dt sigma Uinf / (1+s)
     const T* Ub; const T* Vb; const T* DxOb; const T* DyOb;   // base-derived fields
     Cx<T>* X1; Cx<T>* X2;  // x-spectral, y-physical [kx][y]
+    Cx<T>* X3;             // x-spectrum of v (kVel steppers)
     Cx<T>* Wh; Cx<T>* Nh;  // full spectra [kx][ky]
     const T* tA; const T* tB; const T* tP;   // spectral operator tables [nxh+1][ny]
+    const T* tDx; const T* tDy;              // sin(2 pi kx/nx)/dx [nxh+1], sin(2 pi ky/ny)/dy [ny]
     const Cx<T>* twx[4]; const Cx<T>* twy[4];   // per-pass twiddle tables for LE = 1, 2, 3
 };
 
@@ -68,6 +99,11 @@ template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
     if (f.Y) f.Y += fo;
     f.X1 += co;
     f.X2 += co;
+    if (kF32<T>) {
+        f.U += fo;
+        f.V += fo;
+        f.X3 += co;
+    }
     f.Wh += co;
     f.Nh += co;
     f.cS += so;
@@ -83,8 +119,9 @@ template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
     return true;
 }
 
-// Diagonal operators at (kx, ky), kx in [0, nx/2]: Crank-Nicolson A = a/b,
-// B = dt/b (both times the 1/(nx ny) of the inverse transform) and the
+// Diagonal operators at (kx, ky), kx in [0, nx/2]: Crank-Nicolson A = a/b
+// (FP32 steppers: A - 1), B = dt/b (both times the 1/(nx ny) of the inverse
+// transform) and the
 // inverse Laplacian P = -1/lam (zero for the mean mode), read from tables
 // computed on the host in FP64 and rounded once to the stepper's precision
 // (a division costs ~10 FP64 instructions on GB300, and evaluating them in
@@ -114,36 +151,51 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
         return f.W[c];
     } else if (MODE == FWD_RHS_NL || MODE == FWD_RHS_LIN) {
         const T* W = f.W;
-        const T* P = f.P;
         const T dxw = (W[(size_t)j * nx + ip] - W[(size_t)j * nx + im]) * f.idx2;
         const T dyw = (W[(size_t)jp * nx + i] - W[(size_t)jm * nx + i]) * f.idy2;
-        const T dyp = (P[(size_t)jp * nx + i] - P[(size_t)jm * nx + i]) * f.idy2;
-        const T dxp = (P[(size_t)j * nx + ip] - P[(size_t)j * nx + im]) * f.idx2;
+        T up, vp;   // u' = D_y psi, v = -D_x psi at (i, j)
+        if (kF32<T>) {
+            up = f.U[c];
+            vp = f.V[c];
+        } else {
+            const T* P = f.P;
+            up = (P[(size_t)jp * nx + i] - P[(size_t)jm * nx + i]) * f.idy2;
+            vp = -((P[(size_t)j * nx + ip] - P[(size_t)j * nx + im]) * f.idx2);
+        }
         if (MODE == FWD_RHS_NL) {
-            const T u = f.Uinf + dyp;
-            const T v = -dxp;
-            return -(u * dxw + v * dyw);
+            const T u = f.Uinf + up;
+            return -(u * dxw + vp * dyw);
         } else {
             // N' = -(U_b D_x w + V_b D_y w + u' D_x Om_b + v' D_y Om_b)
-            return -(f.Ub[c] * dxw + f.Vb[c] * dyw + dyp * f.DxOb[c] - dxp * f.DyOb[c]);
+            return -(f.Ub[c] * dxw + f.Vb[c] * dyw + up * f.DxOb[c] + vp * f.DyOb[c]);
         }
     } else {
         // omega^{n+1} = omega* + D_x dv - D_y du with the implicit Brinkman +
         // fringe velocity correction du = cG - cS u*, dv = -cS v*.
-        const T* P = f.P;
         const T U = (MODE == FWD_PEN_NL) ? f.Uinf : T(0);
-        const int ipp = (i + 2) & (nx - 1), imm = (i - 2) & (nx - 1);
-        const int jpp = (j + 2) & (ny - 1), jmm = (j - 2) & (ny - 1);
         const size_t rj = (size_t)j * nx;
-        // v* at (i+1, j) and (i-1, j)
-        const T vp = -((P[rj + ipp] - P[rj + i]) * f.idx2);
-        const T vm = -((P[rj + i] - P[rj + imm]) * f.idx2);
+        const size_t cp = (size_t)jp * nx + i, cm = (size_t)jm * nx + i;
+        // v* at (i+1, j) and (i-1, j), u* at (i, j+1) and (i, j-1)
+        const T* P = f.P;
+        T vp, vm, up, um;
+        if (kF32<T>) {
+            vp = f.V[rj + ip];
+            vm = f.V[rj + im];
+        } else {
+            const int ipp = (i + 2) & (nx - 1), imm = (i - 2) & (nx - 1);
+            vp = -((P[rj + ipp] - P[rj + i]) * f.idx2);
+            vm = -((P[rj + i] - P[rj + imm]) * f.idx2);
+        }
         const T dvp = -f.cS[rj + ip] * vp;
         const T dvm = -f.cS[rj + im] * vm;
-        // u* at (i, j+1) and (i, j-1)
-        const size_t cp = (size_t)jp * nx + i, cm = (size_t)jm * nx + i;
-        const T up = U + (P[(size_t)jpp * nx + i] - P[c]) * f.idy2;
-        const T um = U + (P[c] - P[(size_t)jmm * nx + i]) * f.idy2;
+        if (kF32<T>) {
+            up = U + f.U[cp];
+            um = U + f.U[cm];
+        } else {
+            const int jpp = (j + 2) & (ny - 1), jmm = (j - 2) & (ny - 1);
+            up = U + (P[(size_t)jpp * nx + i] - P[c]) * f.idy2;
+            um = U + (P[c] - P[(size_t)jmm * nx + i]) * f.idy2;
+        }
         T dup = -f.cS[cp] * up;
         T dum = -f.cS[cm] * um;
         if (MODE == FWD_PEN_NL) {
@@ -230,21 +282,36 @@ __global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool
     }
 }
 
-// Inverse x-transform of RP row pairs per block.  same: pair p = rows
-// (2p, 2p+1) of XA -> dA; otherwise pair p = row p of XA -> dA and row p of
-// XB -> dB.
-template <class T, int LE>
-__global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP, bool same) {
+// What an inverse row pass transforms.  Each complex transform carries two
+// real rows: either rows (2p, 2p+1) of one array (a "same" pass) or row p of
+// two arrays.
+enum InvIO {
+    INV_PSI = 0,   // X2 row pairs -> P
+    INV_WP = 1,    // X1 -> W, X2 -> P, row by row
+    INV_UV = 2,    // X2 -> U, X3 -> V, row by row
+    INV_WUV = 3,   // blocks over rows [0, ny): X1 -> W, X2 -> U; then X3 row pairs -> V
+};
+
+// Inverse x-transform of RP sequences per block, as selected by IO.
+template <class T, int LE, int IO>
+__global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP) {
     using C = Cx<T>;
     if (!member_view(f)) return;
-    const C* XA = same ? f.X2 : f.X1;
-    const C* XB = f.X2;
-    T* dA = same ? f.P : f.W;
-    T* dB = f.P;
+    int pair0 = blockIdx.x * RP;
+    bool same = (IO == INV_PSI);
+    const C* XA = (IO == INV_PSI || IO == INV_UV) ? f.X2 : f.X1;
+    const C* XB = (IO == INV_UV) ? f.X3 : f.X2;
+    T* dA = (IO == INV_PSI) ? f.P : (IO == INV_UV) ? f.U : f.W;
+    T* dB = (IO == INV_UV) ? f.V : (IO == INV_WUV) ? f.U : f.P;
+    if (IO == INV_WUV && pair0 >= f.ny) {   // RP divides ny/2: a block lies wholly in one part
+        same = true;
+        pair0 -= f.ny;
+        XA = XB = f.X3;
+        dA = dB = f.V;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int nx = f.nx, ny = f.ny, nh = nx >> 1, S = seq_stride(nx, RP, (int)sizeof(C) / 4);
-    const int pair0 = blockIdx.x * RP;
     constexpr int E = 1 << LE;   // RP*nh spectra over RP*nx/E threads: E/2 each
     C Av[E / 2], Bv[E / 2];
 #pragma unroll
@@ -299,8 +366,13 @@ __device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
 }
 
 // Forward y-transform of CP columns of X1, store Wh, psi^ = scale * tP * omega^,
-// inverse y-transform into X2.
-template <class T, int LE>
+// inverse y-transform into X2.  VEL: inverse y-transforms of
+// u'^ = i sy psi^ into X2 and v^ = -i sx psi^ into X3 instead, with
+// sy = sin(2 pi ky/ny)/dy, sx = sin(2 pi kx/nx)/dx, the symbols of the
+// centred differences (zero at kx = 0 and kx = nx/2, so the packed column of
+// v is zero; sy is odd in ky and acts alike on both halves of the packed
+// column).
+template <class T, int LE, bool VEL>
 __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     using C = Cx<T>;
     if (!member_view(f)) return;
@@ -308,6 +380,7 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     C* s = reinterpret_cast<C*>(smem_raw);
     const int ny = f.ny, logy = f.logy;
     const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
+    C* s2 = s + (size_t)CP * S;   // VEL: v^
     const int c0 = blockIdx.x * CP;
     constexpr int E = 1 << LE;   // CP*ny values over CP*ny/E threads: E each
     {
@@ -332,27 +405,44 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
         const int kx = c0 + c;
         C* z = s + c * S;
         if (kx != 0) {
-            z[sw<T>(k)] = cscale(z[sw<T>(k)], scale * SpecOp<T>::p(f, kx, k));
+            const C ps = cscale(z[sw<T>(k)], scale * SpecOp<T>::p(f, kx, k));
+            if (VEL) {
+                z[sw<T>(k)] = cscale(cmul_pi(ps), f.tDy[k]);
+                s2[c * S + sw<T>(k)] = cscale(cmul_mi(ps), f.tDx[kx]);
+            } else {
+                z[sw<T>(k)] = ps;
+            }
         } else if (k <= (ny >> 1)) {
             const int km = (ny - k) & (ny - 1);
             const T f0 = scale * SpecOp<T>::p(f, 0, k), fN = scale * SpecOp<T>::p(f, f.nxh, k);
             const C zk = z[sw<T>(k)], zm = z[sw<T>(km)];
-            z[sw<T>(k)] = apply_packed0(zk, cconj(zm), f0, fN);
-            if (km != k) z[sw<T>(km)] = apply_packed0(zm, cconj(zk), f0, fN);
+            C pk = apply_packed0(zk, cconj(zm), f0, fN);
+            C pm = apply_packed0(zm, cconj(zk), f0, fN);
+            if (VEL) {
+                pk = cscale(cmul_pi(pk), f.tDy[k]);
+                pm = cscale(cmul_pi(pm), f.tDy[km]);
+                s2[sw<T>(k)] = mk<T>(T(0), T(0));
+                s2[sw<T>(km)] = mk<T>(T(0), T(0));
+            }
+            z[sw<T>(k)] = pk;
+            if (km != k) z[sw<T>(km)] = pm;
         }
     }
     __syncthreads();
-    fft_smem<true, T, LE>(s, logy, S, CP, f.twy[LE]);
+    fft_smem<true, T, LE>(s, logy, S, VEL ? 2 * CP : CP, f.twy[LE]);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
-        f.X2[(size_t)(c0 + c) * ny + j] = s[c * S + sw<T>(j)];
+        const size_t g = (size_t)(c0 + c) * ny + j;
+        f.X2[g] = s[c * S + sw<T>(j)];
+        if (VEL) f.X3[g] = s2[c * S + sw<T>(j)];
     }
 }
 
 // Forward y-transform of N (x-spectra in X1); AB2/AB1 + Crank-Nicolson update
 //   omega*^ = tA omega^ + tB (c1 N^n + c0 N^{n-1}),  psi*^ = tP omega*^
 // (tA, tB carry the 1/(nx ny) of the inverse transform); Nh <- N^n; inverse
-// y-transforms of omega*^ -> X1 and psi*^ -> X2.
+// y-transforms of omega*^ -> X1 and psi*^ -> X2 (kVel: u*'^ -> X2 and
+// v*^ -> X3, as in k_col_poisson).
 template <class T, int LE>
 __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
     using C = Cx<T>;
@@ -392,16 +482,29 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
         const size_t g = (size_t)kx * ny + k;
         C* z1 = s1 + c * S;
         C* z2 = s2 + c * S;
-        const C* z3 = s3 + c * S;
+        C* z3 = s3 + c * S;
         if (kx != 0) {
             const C nn = z1[sw<T>(k)];
             const C r = first ? cscale(nn, c1) : cadd(cscale(nn, c1), cscale(z3[sw<T>(k)], c0));
             f.Nh[g] = nn;
             T A, B;
             SpecOp<T>::ab(f, kx, k, A, B);
-            const C ws = cadd(cscale(z2[sw<T>(k)], A), cscale(r, B));
+            C ws;
+            if constexpr (kF32<T>) {   // tA = scale (A - 1): the small terms first, one rounding at the end
+                const C wv = z2[sw<T>(k)];
+                const C t = cadd(cscale(wv, A), cscale(r, B));
+                ws = mk<T>(__fmaf_rn(wv.x, f.scale, t.x), __fmaf_rn(wv.y, f.scale, t.y));
+            } else {
+                ws = cadd(cscale(z2[sw<T>(k)], A), cscale(r, B));
+            }
             z1[sw<T>(k)] = ws;
-            z2[sw<T>(k)] = cscale(ws, SpecOp<T>::p(f, kx, k));
+            const C ps = cscale(ws, SpecOp<T>::p(f, kx, k));
+            if (kF32<T>) {
+                z2[sw<T>(k)] = cscale(cmul_pi(ps), f.tDy[k]);
+                z3[sw<T>(k)] = cscale(cmul_mi(ps), f.tDx[kx]);
+            } else {
+                z2[sw<T>(k)] = ps;
+            }
         } else if (k <= (ny >> 1)) {
             const int km = (ny - k) & (ny - 1);
             const C nk = z1[sw<T>(k)], nm = z1[sw<T>(km)];
@@ -418,28 +521,41 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
             SpecOp<T>::ab(f, 0, km, A0m, B0m);
             SpecOp<T>::ab(f, f.nxh, km, ANm, BNm);
             const C wk = z2[sw<T>(k)], wm = z2[sw<T>(km)];
-            const C wsk = cadd(apply_packed0(wk, cconj(wm), A0k, ANk), apply_packed0(rk, cconj(rm), B0k, BNk));
-            const C wsm = cadd(apply_packed0(wm, cconj(wk), A0m, ANm), apply_packed0(rm, cconj(rk), B0m, BNm));
+            C wsk = cadd(apply_packed0(wk, cconj(wm), A0k, ANk), apply_packed0(rk, cconj(rm), B0k, BNk));
+            C wsm = cadd(apply_packed0(wm, cconj(wk), A0m, ANm), apply_packed0(rm, cconj(rk), B0m, BNm));
+            if constexpr (kF32<T>) {   // plus scale * omega^ (tA holds scale (A - 1))
+                wsk = mk<T>(__fmaf_rn(wk.x, f.scale, wsk.x), __fmaf_rn(wk.y, f.scale, wsk.y));
+                wsm = mk<T>(__fmaf_rn(wm.x, f.scale, wsm.x), __fmaf_rn(wm.y, f.scale, wsm.y));
+            }
             z1[sw<T>(k)] = wsk;
             z1[sw<T>(km)] = wsm;
-            z2[sw<T>(k)] = apply_packed0(wsk, cconj(wsm), SpecOp<T>::p(f, 0, k), SpecOp<T>::p(f, f.nxh, k));
-            z2[sw<T>(km)] = apply_packed0(wsm, cconj(wsk), SpecOp<T>::p(f, 0, km), SpecOp<T>::p(f, f.nxh, km));
+            C pk = apply_packed0(wsk, cconj(wsm), SpecOp<T>::p(f, 0, k), SpecOp<T>::p(f, f.nxh, k));
+            C pm = apply_packed0(wsm, cconj(wsk), SpecOp<T>::p(f, 0, km), SpecOp<T>::p(f, f.nxh, km));
+            if (kF32<T>) {
+                pk = cscale(cmul_pi(pk), f.tDy[k]);
+                pm = cscale(cmul_pi(pm), f.tDy[km]);
+                z3[sw<T>(k)] = mk<T>(T(0), T(0));
+                z3[sw<T>(km)] = mk<T>(T(0), T(0));
+            }
+            z2[sw<T>(k)] = pk;
+            z2[sw<T>(km)] = pm;
         }
     }
     __syncthreads();
-    fft_smem<true, T, LE>(s1, logy, S, 2 * CP, f.twy[LE]);
+    fft_smem<true, T, LE>(s1, logy, S, (kF32<T> ? 3 : 2) * CP, f.twy[LE]);
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
         const size_t g = (size_t)(c0i + c) * ny + j;
         f.X1[g] = s1[c * S + sw<T>(j)];
         f.X2[g] = s2[c * S + sw<T>(j)];
+        if (kF32<T>) f.X3[g] = s3[c * S + sw<T>(j)];
     }
 }
 
 // ------------------------------------------------------- pointwise kernels
 
-// Base-derived fields of parameter set blockIdx.y, from Omega_b and Psi_b held
-// in member slot blockIdx.y of W and P.
+// Base-derived fields of parameter set blockIdx.y, from Omega_b and Psi_b
+// (kVel: the base velocity) held in member slot blockIdx.y of W and P (U, V).
 template <class T>
 __global__ void k_base_fields(Fields<T> f, T* Ub, T* Vb, T* DxOb, T* DyOb) {
     const size_t n = (size_t)f.nx * f.ny;
@@ -451,8 +567,13 @@ __global__ void k_base_fields(Fields<T> f, T* Ub, T* Vb, T* DxOb, T* DyOb) {
         const int j = (int)(c >> f.logx);
         const int ip = (i + 1) & (f.nx - 1), im = (i - 1) & (f.nx - 1);
         const int jp = (j + 1) & (f.ny - 1), jm = (j - 1) & (f.ny - 1);
-        Ub[off + c] = f.Uinf + (P[(size_t)jp * f.nx + i] - P[(size_t)jm * f.nx + i]) * f.idy2;
-        Vb[off + c] = -((P[(size_t)j * f.nx + ip] - P[(size_t)j * f.nx + im]) * f.idx2);
+        if (kF32<T>) {   // u', v of the base in U, V
+            Ub[off + c] = f.Uinf + f.U[off + c];
+            Vb[off + c] = f.V[off + c];
+        } else {
+            Ub[off + c] = f.Uinf + (P[(size_t)jp * f.nx + i] - P[(size_t)jm * f.nx + i]) * f.idy2;
+            Vb[off + c] = -((P[(size_t)j * f.nx + ip] - P[(size_t)j * f.nx + im]) * f.idx2);
+        }
         DxOb[off + c] = (W[(size_t)j * f.nx + ip] - W[(size_t)j * f.nx + im]) * f.idx2;
         DyOb[off + c] = (W[(size_t)jp * f.nx + i] - W[(size_t)jm * f.nx + i]) * f.idy2;
     }
@@ -525,8 +646,11 @@ static const size_t kMaxSmem = 200 * 1024;
 #define K_FWD_RLIN(le) k_row_forward<T, FWD_RHS_LIN, le>
 #define K_FWD_PNL(le) k_row_forward<T, FWD_PEN_NL, le>
 #define K_FWD_PLIN(le) k_row_forward<T, FWD_PEN_LIN, le>
-#define K_INV(le) k_row_inverse<T, le>
-#define K_COLP(le) k_col_poisson<T, le>
+#define K_INVP(le) k_row_inverse<T, le, (kF32<T> ? INV_UV : INV_PSI)>
+#define K_INVR(le) k_row_inverse<T, le, (kF32<T> ? INV_WUV : INV_WP)>
+#define K_INVPSI(le) k_row_inverse<T, le, INV_PSI>
+#define K_COLP(le) k_col_poisson<T, le, kF32<T>>
+#define K_COLPSI(le) k_col_poisson<T, le, false>
 #define K_COLU(le) k_col_update<T, le>
 
 template <class T>
@@ -549,6 +673,7 @@ class StepperImpl : public StepperBase {
     int poisson(const double* omega, double* psi) override;
     int step_nonlinear(double* omega, int nsteps) override;
     int set_base(const double* base_omega) override;
+    int set_base_ptrs(const double* const* base_omegas) override;
     int step_linear(const double* v_in, double* v_out, int nsteps) override;
     int step_linear_ptrs(const double* const* in, double* const* out, int nsteps) override;
     int residual(const double* q, double* r) override;
@@ -633,7 +758,8 @@ class StepperImpl : public StepperBase {
     int launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first);
     int launch_plain(cudaStream_t st);
     int transform_W();                                   // X1 = x-spectrum of W
-    int stream_function(cudaStream_t st);                // Wh, X2, P from X1
+    int stream_function(cudaStream_t st);                // Wh, X2 (X3), P (U, V) from X1
+    int psi_function(cudaStream_t st);                   // Wh, X2, P from X1
     int issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last);
     int run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1 = true);
     int sumsq_diff(const T* a, const T* b, double* out);   // out[B]
@@ -642,14 +768,28 @@ class StepperImpl : public StepperBase {
 
 // ---------------------------------------------------------- launch plans
 
+// Transforms per member of launch kid: row pairs or rows for the row passes
+// (see InvIO), columns for the column passes.
+template <class T> static int seq_count(int kid, int nx, int ny) {
+    switch (kid) {
+        case KCOLP:
+        case KCOLU: return nx / 2;
+        case KINVP: return kF32<T> ? ny : ny / 2;
+        case KINVR: return kF32<T> ? ny + ny / 2 : ny;
+        default: return ny / 2;
+    }
+}
+
 template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) const {
     Launch L;
     const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
     const int N = row ? nx_ : ny_;
     const int logN = row ? ilog2(nx_) : ilog2(ny_);
-    const int count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;   // sequences per member
-    const int nseq_smem = (kid == KCOLU) ? 3 : 1;                     // smem sequences per unit
+    const int count = seq_count<T>(kid, nx_, ny_);
+    // shared-memory sequences per unit
+    const int nseq_smem = (kid == KCOLU) ? 3 : (kid == KCOLP && kF32<T>) ? 2 : 1;
     if (le < 1 || le > 3 || logN < le || per < 1 || !is_pow2(per) || per > count) return L;
+    if (kF32<T> && kid == KINVR && per > ny_ / 2) return L;   // blocks must not straddle the two parts
     const int threads = per * (N >> le);
     const int rp = row ? per : ((N >> le) < 32 ? 32 / (N >> le) : 1);
     const size_t smem = (size_t)per * nseq_smem * seq_stride(N, rp, (int)sizeof(C) / 4) * sizeof(C);
@@ -670,7 +810,7 @@ template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) co
 template <class T> Launch StepperImpl<T>::default_plan(int kid) const {
     const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
     const int N = row ? nx_ : ny_;
-    const long count = row ? (kid == KINVR ? ny_ : ny_ / 2) : nxh_;
+    const long count = seq_count<T>(kid, nx_, ny_);
     const long target = 4L * 152 * 32;   // one warp per SM sub-partition
     int le = 3;
     while (le > 2 && (long)B_ * count * (N >> le) < target) --le;
@@ -693,9 +833,9 @@ template <class T> int StepperImpl<T>::set_smem_attr(int kid, const Launch& L) {
         default: NS_ATTR(KERNEL(3)); break; \
     }
     switch (kid) {
-        case KCOLP: NS_ATTR_LE(K_COLP); break;
-        case KINVP:
-        case KINVR: NS_ATTR_LE(K_INV); break;
+        case KCOLP: NS_ATTR_LE(K_COLP); NS_ATTR_LE(K_COLPSI); break;
+        case KINVP: NS_ATTR_LE(K_INVP); NS_ATTR_LE(K_INVPSI); break;
+        case KINVR: NS_ATTR_LE(K_INVR); break;
         case KFWDR: NS_ATTR_LE(K_FWD_RNL); NS_ATTR_LE(K_FWD_RLIN); NS_ATTR_LE(K_FWD_PLAIN); break;
         case KCOLU: NS_ATTR_LE(K_COLU); break;
         default: NS_ATTR_LE(K_FWD_PNL); NS_ATTR_LE(K_FWD_PLIN); break;
@@ -719,9 +859,9 @@ template <class T> int max_threads_for(int kid, int le) {
         default: take((const void*)KERNEL(3)); break; \
     }
     switch (kid) {
-        case KCOLP: NS_TAKE_LE(K_COLP); break;
-        case KINVP:
-        case KINVR: NS_TAKE_LE(K_INV); break;
+        case KCOLP: NS_TAKE_LE(K_COLP); NS_TAKE_LE(K_COLPSI); break;
+        case KINVP: NS_TAKE_LE(K_INVP); NS_TAKE_LE(K_INVPSI); break;
+        case KINVR: NS_TAKE_LE(K_INVR); break;
         case KFWDR: NS_TAKE_LE(K_FWD_RNL); NS_TAKE_LE(K_FWD_RLIN); NS_TAKE_LE(K_FWD_PLAIN); break;
         case KCOLU: NS_TAKE_LE(K_COLU); break;
         default: NS_TAKE_LE(K_FWD_PNL); NS_TAKE_LE(K_FWD_PLIN); break;
@@ -740,11 +880,6 @@ template <class T> int StepperImpl<T>::set_plan(int kid, int le, int per) {
         return NSSTAB_ERR_INVALID_ARG;
     }
     NS_TRY(set_smem_attr(kid, L));
-    // the inverse-row kernel serves two launches: keep the larger smem attribute
-    if (kid == KINVP || kid == KINVR) {
-        const Launch& o = plan_[kid == KINVP ? KINVR : KINVP];
-        if (o.ok && o.le == L.le && o.smem > L.smem) NS_TRY(set_smem_attr(kid, o));
-    }
     plan_[kid] = L;
     clear_graphs();
     return NSSTAB_OK;
@@ -771,12 +906,12 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
     const dim3 g(L.blocks, B_);
     switch (kid) {
         case KCOLP: {
-#define CALL_COLP(le) k_col_poisson<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, scale_)
+#define CALL_COLP(le) k_col_poisson<T, le, kF32<T>><<<g, L.threads, L.smem, st>>>(f_, L.per, scale_)
             NS_DISPATCH_LE(L, CALL_COLP);
             break;
         }
         case KINVP: {
-#define CALL_INVP(le) k_row_inverse<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, true)
+#define CALL_INVP(le) K_INVP(le)<<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper)
             NS_DISPATCH_LE(L, CALL_INVP);
             break;
         }
@@ -797,7 +932,7 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
             break;
         }
         case KINVR: {
-#define CALL_INVR(le) k_row_inverse<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false)
+#define CALL_INVR(le) K_INVR(le)<<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper)
             NS_DISPATCH_LE(L, CALL_INVR);
             break;
         }
@@ -833,7 +968,12 @@ template <class T> int StepperImpl<T>::build_tables() {
             for (int r = 0; r < R; ++r)
                 for (int k = 0; k < Ns; ++k) {
                     const long double a = two_pi * (long double)(r * k) / (long double)(Ns * R);
-                    out.push_back(mk<T>((T)(double)cosl(a), (T)(double)(-sinl(a))));
+                    const long double c = cosl(a), sn = -sinl(a);
+                    const T ch = (T)(double)c, sh = (T)(double)sn;
+                    out.push_back(mk<T>(ch, sh));
+                    if (kTwWidth<T> == 2)   // FP32: the rounding errors of hi, next to it
+                        out.push_back(mk<T>((T)(double)(c - (long double)(double)ch),
+                                            (T)(double)(sn - (long double)(double)sh)));
                 }
             nsl += LR;
             rem -= LR;
@@ -856,13 +996,15 @@ template <class T> int StepperImpl<T>::build_tables() {
             tP[g] = (kx == 0 && ky == 0) ? T(0) : (T)(-1.0 / lam);
             for (int k = 0; k < S_; ++k) {
                 const double nu = 1.0 / Re_[k];
-                if (kx == 0 && ky == 0) {
-                    tA[k * nt + g] = tB[k * nt + g] = T(0);
+                if (kx == 0 && ky == 0) {   // the mean mode is removed: A = B = 0
+                    tA[k * nt + g] = kF32<T> ? (T)(-scale) : T(0);
+                    tB[k * nt + g] = T(0);
                     continue;
                 }
                 const double a = 1.0 + 0.5 * nu * dt * lam;
                 const double b = 1.0 - 0.5 * nu * dt * lam;
-                tA[k * nt + g] = (T)(scale * a / b);
+                // FP32: A - 1 = nu dt lam / b, formed without cancellation
+                tA[k * nt + g] = kF32<T> ? (T)(scale * (nu * dt * lam) / b) : (T)(scale * a / b);
                 tB[k * nt + g] = (T)(scale * dt / b);
             }
         }
@@ -916,6 +1058,14 @@ template <class T> int StepperImpl<T>::build_tables() {
     NS_CUDA(cudaMemcpyAsync((void*)f_.tA, tA.data(), tA.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaMemcpyAsync((void*)f_.tB, tB.data(), tB.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaMemcpyAsync((void*)f_.tP, tP.data(), tP.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    // centred-difference symbols: D_x <-> i sin(2 pi kx/nx)/dx, D_y alike
+    std::vector<T> tDx(nxh + 1), tDy(ny);
+    for (int kx = 0; kx <= nxh; ++kx) tDx[kx] = (kx == 0 || kx == nxh) ? T(0) : (T)(std::sin(2.0 * kPi * kx / nx) / dx);
+    for (int ky = 0; ky < ny; ++ky) tDy[ky] = (2 * ky == ny || ky == 0) ? T(0) : (T)(std::sin(2.0 * kPi * ky / ny) / dy);
+    if (f_.tDx) {
+        NS_CUDA(cudaMemcpyAsync((void*)f_.tDx, tDx.data(), tDx.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+        NS_CUDA(cudaMemcpyAsync((void*)f_.tDy, tDy.data(), tDy.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
+    }
     NS_CUDA(cudaMemcpyAsync((void*)f_.cS, cS.data(), cS.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaMemcpyAsync((void*)f_.cG, cG.data(), cG.size() * sizeof(T), cudaMemcpyHostToDevice, stream_));
     NS_CUDA(cudaStreamSynchronize(stream_));   // host vectors go out of scope
@@ -942,6 +1092,7 @@ template <class T> int StepperImpl<T>::init() {
     f_.idy2 = (T)(1.0 / (2.0 * cfg_.Ly / ny_));
     f_.Uinf = (T)cfg_.Uinf;
     scale_ = (T)(1.0 / ((double)nx_ * (double)ny_));
+    f_.scale = scale_;
     const size_t B = B_, S = S_;
     T *W, *P, *cS, *cG, *tA, *tB, *tP;
     C *X1, *X2, *Wh, *Nh;
@@ -956,10 +1107,23 @@ template <class T> int StepperImpl<T>::init() {
     NS_TRY(dalloc(&tA, S * nt));
     NS_TRY(dalloc(&tB, S * nt));
     NS_TRY(dalloc(&tP, nt));
+    if (kF32<T>) {
+        T *U, *V, *tDx, *tDy;
+        C* X3;
+        NS_TRY(dalloc(&U, B * n_));
+        NS_TRY(dalloc(&V, B * n_));
+        NS_TRY(dalloc(&X3, B * nc_));
+        NS_TRY(dalloc(&tDx, (size_t)nxh_ + 1));
+        NS_TRY(dalloc(&tDy, (size_t)ny_));
+        f_.U = U; f_.V = V; f_.X3 = X3; f_.tDx = tDx; f_.tDy = tDy;
+        NS_CUDA(cudaMemsetAsync(U, 0, B * n_ * sizeof(T), stream_));
+        NS_CUDA(cudaMemsetAsync(V, 0, B * n_ * sizeof(T), stream_));
+        NS_CUDA(cudaMemsetAsync(X3, 0, B * nc_ * sizeof(C), stream_));
+    }
     for (int le = 1; le <= 3; ++le) {
         C *tx, *ty;
-        NS_TRY(dalloc(&tx, (size_t)2 * nx_));
-        NS_TRY(dalloc(&ty, (size_t)2 * ny_));
+        NS_TRY(dalloc(&tx, (size_t)2 * kTwWidth<T> * nx_));
+        NS_TRY(dalloc(&ty, (size_t)2 * kTwWidth<T> * ny_));
         f_.twx[le] = tx;
         f_.twy[le] = ty;
     }
@@ -1043,6 +1207,29 @@ template <class T> int StepperImpl<T>::transform_W() { return launch_plain(strea
 template <class T> int StepperImpl<T>::stream_function(cudaStream_t st) {
     NS_TRY(launch(KCOLP, st, false, false, true, false));
     return launch(KINVP, st, false, false, true, false);
+}
+
+// P = psi from X1 for every stepper (kVel steppers carry u', v in the step
+// and form psi only here): the psi variant of the column pass, then the
+// row pairs of X2, with the launch shapes of KCOLP and KINVP.
+template <class T> int StepperImpl<T>::psi_function(cudaStream_t st) {
+    if (!kF32<T>) return stream_function(st);
+    const Launch& Lc = plan_[KCOLP];
+    const dim3 gc(Lc.blocks, B_);
+#define CALL_COLPSI(le) k_col_poisson<T, le, false><<<gc, Lc.threads, Lc.smem, st>>>(f_, Lc.per, scale_)
+    NS_DISPATCH_LE(Lc, CALL_COLPSI);
+    NS_LAUNCH_CHECK();
+    Launch L = plan_[KINVP];   // ny rows -> ny/2 row pairs, each block at most as large
+    while (L.per > ny_ / 2) L.per /= 2;
+    L.logper = ilog2(L.per);
+    L.blocks = (ny_ / 2) / L.per;
+    L.threads = L.per * (nx_ >> L.le);
+    L.smem = (size_t)L.per * seq_stride(nx_, L.per, (int)sizeof(C) / 4) * sizeof(C);
+    const dim3 gr(L.blocks, B_);
+#define CALL_INVPSI(le) K_INVPSI(le)<<<gr, L.threads, L.smem, st>>>(f_, L.per, L.logper)
+    NS_DISPATCH_LE(L, CALL_INVPSI);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
 }
 
 // Enqueue nsteps time steps on `st`.  first_ab1: the first of them is AB1.
@@ -1151,9 +1338,6 @@ template <class T> int StepperImpl<T>::autotune(int reps, int* chosen) {
             chosen[2 * kid + 1] = best.per;
         }
     }
-    // restore the shared inverse-row smem attribute for both launches
-    NS_TRY(set_plan(KINVP, plan_[KINVP].le, plan_[KINVP].per));
-    NS_TRY(set_plan(KINVR, plan_[KINVR].le, plan_[KINVR].per));
     return NSSTAB_OK;
 }
 
@@ -1196,7 +1380,7 @@ template <class T> int StepperImpl<T>::poisson(const double* omega, double* psi)
     NS_TRY(all_active());
     NS_TRY(gather_contig(omega, B_));
     NS_TRY(transform_W());
-    NS_TRY(stream_function(stream_));
+    NS_TRY(psi_function(stream_));
     return scatter_contig(f_.P, psi);
 }
 
@@ -1211,6 +1395,12 @@ template <class T> int StepperImpl<T>::step_nonlinear(double* omega, int nsteps)
 }
 
 template <class T> int StepperImpl<T>::set_base(const double* base_omega) {
+    std::vector<const double*> p(S_);
+    for (int k = 0; k < S_; ++k) p[k] = base_omega + (size_t)k * n_;
+    return set_base_ptrs(p.data());
+}
+
+template <class T> int StepperImpl<T>::set_base_ptrs(const double* const* base_omegas) {
     if (!f_.Ub) {
         T *Ub, *Vb, *DxOb, *DyOb;
         NS_TRY(dalloc(&Ub, (size_t)S_ * n_));
@@ -1222,11 +1412,15 @@ template <class T> int StepperImpl<T>::set_base(const double* base_omega) {
     }
     // the S base flows go through member slots 0..S-1
     std::vector<unsigned char> a(B_, 0);
-    for (int k = 0; k < S_; ++k) a[k] = 1;
+    std::vector<const double*> src(B_, nullptr);
+    for (int k = 0; k < S_; ++k) {
+        a[k] = 1;
+        src[k] = base_omegas[k];
+    }
     NS_TRY(set_active(a));
-    NS_TRY(gather_contig(base_omega, S_));
+    NS_TRY(gather(src.data()));
     NS_TRY(transform_W());
-    NS_TRY(stream_function(stream_));   // P = Psi_b
+    NS_TRY(stream_function(stream_));   // P = Psi_b (kVel: U, V = its velocity)
     k_base_fields<T><<<dim3(kPtBlocks, S_), 256, 0, stream_>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb, (T*)f_.DyOb);
     NS_LAUNCH_CHECK();
     NS_TRY(all_active());

@@ -42,6 +42,30 @@ class Config(ctypes.Structure):
     ]
 
 
+SERVE_MAX_EIG = 33   # NSSTAB_SERVE_MAX_EIG
+
+
+class EigJob(ctypes.Structure):
+    """Mirror of ``nsstab_eig_job``."""
+
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("dt", ctypes.c_double), ("Re", ctypes.c_double), ("cyl_D", ctypes.c_double),
+        ("base", ctypes.c_void_p), ("v0", ctypes.c_void_p),
+    ]
+
+
+class EigJobResult(ctypes.Structure):
+    """Mirror of ``nsstab_eig_result``."""
+
+    _fields_ = [
+        ("status", ctypes.c_int), ("n_eig", ctypes.c_int), ("n_conv", ctypes.c_int), ("n_matvec", ctypes.c_int),
+        ("group", ctypes.c_int), ("latency_s", ctypes.c_double),
+        ("eig_re", ctypes.c_double * SERVE_MAX_EIG), ("eig_im", ctypes.c_double * SERVE_MAX_EIG),
+        ("resid", ctypes.c_double * SERVE_MAX_EIG),
+    ]
+
+
 # (name, restype, argtypes) of every exported symbol declared in nsstab.h
 SIGNATURES = [
     ("nsstab_config_default", None, [ctypes.POINTER(Config)]),
@@ -72,6 +96,9 @@ SIGNATURES = [
     ("stepper_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     ("stepper_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("stepper_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, _ip]),
+    ("serve_eigs", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(EigJob), ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                                  ctypes.c_int, ctypes.POINTER(EigJobResult), _ip]),
     ("cgs2_orthogonalize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
                                           ctypes.c_void_p, _dp, _dp, ctypes.c_void_p]),
     ("cgs2_orthogonalize_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
@@ -223,6 +250,40 @@ def dense_schur_ordered(A: np.ndarray, thr: float):
     _check(lib.nsstab_dense_schur_ordered(n, A.ctypes.data_as(_dp), float(thr), T.ctypes.data_as(_dp),
                                           Z.ctypes.data_as(_dp), ctypes.byref(p)), "nsstab_dense_schur_ordered")
     return T, Z, p.value
+
+
+def serve_eigs(jobs, m: int, nev: int, tol: float, T: float, max_restarts: int = 0, mem_budget: int = 0,
+               max_concurrent: int = 0, **cfg):
+    """Many eigen-solves on mixed grids (C ``serve_eigs``).
+
+    ``jobs``: list of dicts with keys nx, ny, dt, Re, cyl_D, base, v0 (base
+    and v0 device tensors of shape [ny, nx]).  ``cfg``: shared physical
+    parameters of ``nsstab_config``.  Returns (status, results, ngroups),
+    results a list of dicts (status, mu, residual, n_conv, n_matvec, group,
+    latency_s) in job order."""
+    import torch
+
+    lib = load_library()
+    arr = (EigJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        shape = (int(j["ny"]), int(j["nx"]))
+        arr[i] = EigJob(int(j["nx"]), int(j["ny"]), float(j["dt"]), float(j["Re"]), float(j["cyl_D"]),
+                        _field_ptr(j["base"], shape, "base").value, _field_ptr(j["v0"], shape, "v0").value)
+    out = (EigJobResult * len(jobs))()
+    ng = ctypes.c_int()
+    c = _cfg_from(**cfg)
+    torch.cuda.current_stream().synchronize()   # the call's own streams do not wait on torch's
+    rc = lib.serve_eigs(ctypes.byref(c), len(jobs), arr, int(m), int(nev), float(tol), int(max_restarts), float(T),
+                        int(mem_budget), int(max_concurrent), out, ctypes.byref(ng))
+    if rc < 0 and all(out[i].status == 0 and out[i].n_eig == 0 for i in range(len(jobs))):
+        _check(rc, "serve_eigs")
+    res = []
+    for r in out:
+        k = r.n_eig
+        res.append({"status": r.status, "mu": np.array(r.eig_re[:k]) + 1j * np.array(r.eig_im[:k]),
+                    "residual": np.array(r.resid[:k]), "n_conv": r.n_conv, "n_matvec": r.n_matvec,
+                    "group": r.group, "latency_s": r.latency_s})
+    return rc, res, ng.value
 
 
 @dataclass

@@ -65,6 +65,32 @@ def test_null_arguments_are_rejected(lib):
     assert lib.cgs2_orthogonalize(None, 1, 1, 1, None, None, None, None) == -1
 
 
+@pytest.mark.parametrize("job,kw,what", [
+    (dict(nx=30), {}, "job 1"),             # grid not a power of two
+    (dict(dt=0.03), {}, "job 1"),           # T = 2 is not a whole number of steps
+    (dict(Re=0.0), {}, "job 1"),
+    ({}, dict(nev=40), "nev"),              # nev >= m
+    ({}, dict(T=0.0), "T > 0"),
+])
+def test_serve_eigs_validates_every_job_before_any_device_call(lib, job, kw, what):
+    """The pointers below are never dereferenced: validation fails first."""
+    good = dict(nx=32, ny=16, dt=0.02, Re=50.0, cyl_D=1.0, base=16, v0=16)
+    bad = dict(good, **job)
+    jobs = (nsstab.EigJob * 2)()
+    for i, j in enumerate((good, bad)):
+        jobs[i] = nsstab.EigJob(j["nx"], j["ny"], j["dt"], j["Re"], j["cyl_D"], j["base"], j["v0"])
+    out = (nsstab.EigJobResult * 2)()
+    ng = ctypes.c_int(-7)
+    a = dict(m=40, nev=4, tol=1e-8, max_restarts=1, T=2.0)
+    a.update(kw)
+    cfg = nsstab.config_default()
+    rc = lib.serve_eigs(ctypes.byref(cfg), 2, jobs, a["m"], a["nev"], a["tol"], a["max_restarts"], a["T"], 0, 0,
+                        out, ctypes.byref(ng))
+    assert rc == -1
+    assert what in lib.nsstab_last_error().decode()
+    assert ng.value == -7
+
+
 def _match(a, b):
     return max(np.min(np.abs(b - x)) for x in a)
 
