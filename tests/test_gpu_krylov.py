@@ -141,6 +141,22 @@ def test_fp32_stepper_eigenvalues_within_1e5(small):
         assert np.min(np.abs(mu_dense - mu)) <= 1e-5 * abs(mu)
 
 
+def test_fp32_eigenvalues_track_fp64_on_a_fine_grid():
+    """256x128 (100 steps per product with M): the FP32 stepper's leading
+    eigenvalues stay within 1e-5 relative of the FP64 stepper's, which the
+    tests above pin to the oracle."""
+    nx, ny = 256, 128
+    kw = dict(nx=nx, ny=ny, dt=0.01 * 128 / nx, Re=60.0)
+    base = _dev(inputs.wake_like_field(ny, nx, seed=21))
+    v0 = _dev(inputs.gaussian_field(ny, nx, seed=22))
+    ref = nsstab.Stepper(**kw).arnoldi_eigs(base, v0, m=96, nev=4, tol=1e-9, T=0.5, max_restarts=20)
+    got = nsstab.Stepper(precision=32, **kw).arnoldi_eigs(base, v0, m=96, nev=4, tol=1e-7, T=0.5,
+                                                          max_restarts=20)
+    assert ref.n_conv == len(ref.mu) and got.n_conv == len(got.mu)
+    for mu in got.mu:
+        assert np.min(np.abs(ref.mu - mu)) <= 1e-5 * abs(mu)
+
+
 def test_invalid_krylov_arguments():
     st = nsstab.Stepper(nx=16, ny=8)
     v0 = _dev(inputs.gaussian_field(8, 16, seed=1))
