@@ -313,6 +313,62 @@ int serve_eigs(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, 
                double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
                nsstab_eig_result* results, int* ngroups);
 
+/* ------------------------------------------------------------------------
+ * Learned initial guess for the base-flow solve.
+ *
+ * The paper has no counterpart: the Newton-Krylov fixed-point solve
+ * (Sec. 3.1.2, Eq. 43) converges in fewer iterations from a start closer to
+ * the fixed point, and this network predicts such a start from the flow's
+ * parameters.  It is a 4-level U-Net: at level l (width c_l = width 2^l,
+ * grid (ny, nx) / 2^l) two 3x3 convolutions with periodic wrap + ReLU;
+ * 2x2 average pooling down; nearest 2x upsampling up, concatenated with
+ * the encoder's output of that level (upsampled channels first); a 1x1
+ * output convolution to one channel.  Activations are stored in bfloat16
+ * (round to nearest even), weights as FP32 masters with a bfloat16 copy
+ * used by the convolutions, all sums in FP32.
+ *
+ * Parameters are one flat FP32 vector: for each convolution in the order
+ * enc0a, enc0b, enc1a, enc1b, enc2a, enc2b, enc3a, enc3b, dec2a, dec2b,
+ * dec1a, dec1b, dec0a, dec0b, out, the weight [out][in][3][3] ([1][c_0]
+ * for out) followed by the bias [out].
+ * Fields: x is [B][in_ch][ny][nx] FP32, targets and outputs [B][ny][nx]
+ * FP32, all device memory owned by the caller.  Calls are enqueued on the
+ * network's stream; unet_gradient and unet_train_step synchronise it (they
+ * return the loss).
+ * --------------------------------------------------------------------- */
+typedef struct nsstab_unet nsstab_unet;
+
+/* Number of FP32 parameters of the network (-1 for bad arguments). */
+long unet_param_count(int in_ch, int width);
+
+/* Create a network for inputs of in_ch channels on an ny x nx grid (powers
+ * of two >= 8) and batches of up to max_batch; parameters start at zero.
+ * stream: cudaStream_t as void*.  Errors: INVALID_ARG, OUT_OF_MEMORY. */
+int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* stream, nsstab_unet** out);
+void unet_destroy(nsstab_unet* net);
+
+/* Copy the parameters in (device, unet_param_count floats; also resets
+ * Adam's moments and step count) or out. */
+int unet_set_params(nsstab_unet* net, const float* theta);
+int unet_get_params(nsstab_unet* net, float* theta);
+
+/* y = net(x) for a batch of 1 <= batch <= max_batch.  Asynchronous. */
+int unet_forward(nsstab_unet* net, const float* x, int batch, float* y);
+
+/* Loss = mean over all outputs of (net(x) - target)^2 (host, *loss) and
+ * its gradient with respect to the parameters (device, param_count
+ * floats).  Synchronous. */
+int unet_gradient(nsstab_unet* net, const float* x, const float* target, int batch, float* grad,
+                  double* loss);
+
+/* One Adam step (moments m, v; step t counted from unet_set_params):
+ * m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+ * theta -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps), for the
+ * gradient g of the loss above; *loss is the loss before the step.
+ * Synchronous. */
+int unet_train_step(nsstab_unet* net, const float* x, const float* target, int batch, float lr,
+                    float beta1, float beta2, float eps, double* loss);
+
 /* One CGS2 orthogonalisation (Algorithm 1's Gram-Schmidt step applied
  * twice): h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2;
  * beta = ||w||.  V: device, j columns of length n with leading dimension

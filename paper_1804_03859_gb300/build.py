@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libnsstab.so")
-SOURCES = ["stepper.cu", "stepper_f64.cu", "stepper_f32.cu", "stepper_df64.cu", "krylov.cu", "arnoldi.cu", "capi.cu", "dense_eig.cpp", "noalloc.cu", "newton.cu", "serve.cu"]
+SOURCES = ["stepper.cu", "stepper_f64.cu", "stepper_f32.cu", "stepper_df64.cu", "krylov.cu", "arnoldi.cu", "capi.cu", "dense_eig.cpp", "noalloc.cu", "newton.cu", "serve.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,683 @@
+// The learned initial guess for the Newton-Krylov base-flow solve: a
+// 4-level U-Net (declared in include/nsstab.h; the paper has no network).
+//
+// Storage: activations in bfloat16, channels innermost ([B][H][W][C]), so
+// the channels of one point are one contiguous run; weights as FP32 masters
+// (with Adam's moments) plus a bfloat16 copy that the convolutions read;
+// every sum in FP32; gradients of activations in FP32.
+//
+// Kernels (one pass each, no im2col buffer):
+//   k_conv_fwd       3x3 periodic convolution + bias + ReLU: a thread owns
+//                    one point and 8 output channels; the weights of the
+//                    8 channels for a chunk of 32 input channels are staged
+//                    in shared memory (FP32) and read as broadcasts
+//   k_conv_bwd_data  gradient of the input: the same shape with the roles of
+//                    the channels exchanged and the taps mirrored
+//   k_conv_bwd_w     gradient of the weights and bias: a block owns a 16 x 16
+//                    (output, input channel) tile and a chunk of points,
+//                    9 tap sums per thread, added to the FP32 gradient
+//   pooling, upsampling with concatenation, their adjoints, the 1x1 output
+//   layer, the mean-squared loss and Adam are pointwise kernels.
+// The layer sequence and every rounding point follow the oracle's
+// definition of the network (the same flat parameter layout).
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace nsstab {
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int kLevels = 4;
+constexpr int kCoTile = 8;      // output channels per thread in k_conv_fwd
+constexpr int kCiChunk = 32;    // input channels per shared-memory stage
+constexpr int kFwdThreads = 128;
+
+struct ConvDesc {
+    int ci = 0, co = 0, k = 3;   // k = 3 (3x3) or 1 (the output layer)
+    long w_off = 0, b_off = 0;   // offsets into the flat parameter vector
+};
+
+// Neighbour (y + dy, x + dx) of point p = (b, y, x) on the periodic
+// 2^lh x 2^lw grid.
+__device__ __forceinline__ long nbr(long p, int lh, int lw, int dy, int dx) {
+    const int W = 1 << lw, H = 1 << lh;
+    const int x = (int)(p & (W - 1));
+    const int y = (int)((p >> lw) & (H - 1));
+    const long b = p >> (lw + lh);
+    return (((b << lh) + ((y + dy) & (H - 1))) << lw) + ((x + dx) & (W - 1));
+}
+
+// out[p][co] = relu(bias[co] + sum_{tap, ci} w[co][ci][tap] in[nbr(p, tap)][ci])
+__global__ void k_conv_fwd(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
+                           bf16* __restrict__ out, long P, int lh, int lw, int Ci, int Co) {
+    __shared__ float ws[9][kCiChunk][kCoTile];
+    const long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int co0 = blockIdx.y * kCoTile;
+    float acc[kCoTile];
+#pragma unroll
+    for (int c = 0; c < kCoTile; ++c) acc[c] = (co0 + c < Co) ? bias[co0 + c] : 0.f;
+    long nb[9];
+    if (p < P) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) nb[t] = nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci;
+    }
+    for (int c0 = 0; c0 < Ci; c0 += kCiChunk) {
+        const int nci = min(kCiChunk, Ci - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 9 * kCiChunk * kCoTile; e += blockDim.x) {
+            const int c = e % kCoTile, ci = (e / kCoTile) % kCiChunk, t = e / (kCoTile * kCiChunk);
+            const int co = co0 + c;
+            ws[t][ci][c] = (ci < nci && co < Co) ? __bfloat162float(w[((long)co * Ci + c0 + ci) * 9 + t]) : 0.f;
+        }
+        __syncthreads();
+        if (p < P) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const bf16* src = in + nb[t] + c0;
+                for (int ci = 0; ci < nci; ++ci) {
+                    const float a = __bfloat162float(src[ci]);
+#pragma unroll
+                    for (int c = 0; c < kCoTile; ++c) acc[c] = fmaf(a, ws[t][ci][c], acc[c]);
+                }
+            }
+        }
+    }
+    if (p < P) {
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c)
+            if (co0 + c < Co) out[p * Co + co0 + c] = __float2bfloat16_rn(fmaxf(acc[c], 0.f));
+    }
+}
+
+// gin[q][ci] = sum_{tap, co} w[co][ci][tap] gz[q - tap offset][co]
+__global__ void k_conv_bwd_data(const float* __restrict__ gz, const bf16* __restrict__ w, float* __restrict__ gin,
+                                long P, int lh, int lw, int Ci, int Co) {
+    __shared__ float ws[9][kCiChunk][kCoTile];   // [tap][co in chunk][ci in tile]
+    const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int ci0 = blockIdx.y * kCoTile;
+    float acc[kCoTile];
+#pragma unroll
+    for (int c = 0; c < kCoTile; ++c) acc[c] = 0.f;
+    long nb[9];
+    if (q < P) {
+#pragma unroll
+        for (int t = 0; t < 9; ++t) nb[t] = nbr(q, lh, lw, 1 - t / 3, 1 - t % 3) * Co;
+    }
+    for (int c0 = 0; c0 < Co; c0 += kCiChunk) {
+        const int nco = min(kCiChunk, Co - c0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 9 * kCiChunk * kCoTile; e += blockDim.x) {
+            const int c = e % kCoTile, co = (e / kCoTile) % kCiChunk, t = e / (kCoTile * kCiChunk);
+            const int ci = ci0 + c;
+            ws[t][co][c] = (co < nco && ci < Ci) ? __bfloat162float(w[((long)(c0 + co) * Ci + ci) * 9 + t]) : 0.f;
+        }
+        __syncthreads();
+        if (q < P) {
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+                const float* src = gz + nb[t] + c0;
+                for (int co = 0; co < nco; ++co) {
+                    const float g = src[co];
+#pragma unroll
+                    for (int c = 0; c < kCoTile; ++c) acc[c] = fmaf(g, ws[t][co][c], acc[c]);
+                }
+            }
+        }
+    }
+    if (q < P) {
+#pragma unroll
+        for (int c = 0; c < kCoTile; ++c)
+            if (ci0 + c < Ci) gin[q * Ci + ci0 + c] = acc[c];
+    }
+}
+
+// gw[co][ci][tap] += sum_p gz[p][co] in[nbr(p, tap)][ci]; gb[co] += sum_p gz[p][co]
+// blockDim = 256: thread (co_l, ci_l) = (tid / 16, tid % 16) of the block's tile.
+__global__ void k_conv_bwd_w(const float* __restrict__ gz, const bf16* __restrict__ in, float* __restrict__ gw,
+                             float* __restrict__ gb, long P, int lh, int lw, int Ci, int Co, long chunk) {
+    const int ci_tiles = (Ci + 15) / 16;
+    const int co = (blockIdx.x / ci_tiles) * 16 + threadIdx.x / 16;
+    const int ci = (blockIdx.x % ci_tiles) * 16 + threadIdx.x % 16;
+    const long p0 = blockIdx.y * chunk, p1 = min(P, p0 + chunk);
+    if (co >= Co || ci >= Ci) return;
+    float acc[9], accb = 0.f;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.f;
+    const bool do_b = (ci == 0);
+    for (long p = p0; p < p1; ++p) {
+        const float g = gz[p * Co + co];
+        if (do_b) accb += g;
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+            acc[t] = fmaf(g, __bfloat162float(in[nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci]), acc[t]);
+    }
+#pragma unroll
+    for (int t = 0; t < 9; ++t) atomicAdd(&gw[((long)co * Ci + ci) * 9 + t], acc[t]);
+    if (do_b) atomicAdd(&gb[co], accb);
+}
+
+// x [B][C][H][W] FP32 -> [B][H][W][C] bfloat16
+__global__ void k_to_nhwc(const float* __restrict__ x, bf16* __restrict__ out, long P, int HW, int C) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P * C; e += (long)gridDim.x * blockDim.x) {
+        const long p = e / C;
+        const int c = (int)(e % C);
+        const long b = p / HW, s = p % HW;
+        out[e] = __float2bfloat16_rn(x[(b * C + c) * HW + s]);
+    }
+}
+
+// 2x2 mean of [B][H][W][C] -> [B][H/2][W/2][C], rounded to bfloat16
+__global__ void k_pool(const bf16* __restrict__ in, bf16* __restrict__ out, long Pout, int Ho, int Wo, int C) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < Pout * C; e += (long)gridDim.x * blockDim.x) {
+        const long p = e / C;
+        const int c = (int)(e % C);
+        const int x = (int)(p % Wo);
+        const long r = p / Wo;
+        const int y = (int)(r % Ho);
+        const long b = r / Ho;
+        const int W = 2 * Wo;
+        const long i00 = ((b * 2 * Ho + 2 * y) * W + 2 * x) * C + c;
+        const float s = __bfloat162float(in[i00]) + __bfloat162float(in[i00 + C]) +
+                        __bfloat162float(in[i00 + (long)W * C]) + __bfloat162float(in[i00 + (long)W * C + C]);
+        out[e] = __float2bfloat16_rn(0.25f * s);
+    }
+}
+
+// out[b][y][x] = (low[b][y/2][x/2][0..C1), skip[b][y][x][0..C2))
+__global__ void k_up_cat(const bf16* __restrict__ low, const bf16* __restrict__ skip, bf16* __restrict__ out,
+                         long P, int H, int W, int C1, int C2) {
+    const int C = C1 + C2;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P * C; e += (long)gridDim.x * blockDim.x) {
+        const long p = e / C;
+        const int c = (int)(e % C);
+        if (c < C1) {
+            const int x = (int)(p % W);
+            const long r = p / W;
+            const int y = (int)(r % H);
+            const long b = r / H;
+            out[e] = low[((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C1 + c];
+        } else {
+            out[e] = skip[p * C2 + (c - C1)];
+        }
+    }
+}
+
+// adjoint of k_up_cat: glow[q][c] = sum over the 2x2 children of g[.][c];
+// gskip[p][c] = g[p][C1 + c]
+__global__ void k_up_cat_bwd(const float* __restrict__ g, float* __restrict__ glow, float* __restrict__ gskip,
+                             long Plow, int Hl, int Wl, int C1, int C2) {
+    const int C = C1 + C2, W = 2 * Wl;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < Plow * C; e += (long)gridDim.x * blockDim.x) {
+        const long q = e / C;
+        const int c = (int)(e % C);
+        const int x = (int)(q % Wl);
+        const long r = q / Wl;
+        const int y = (int)(r % Hl);
+        const long b = r / Hl;
+        const long p00 = (b * 2 * Hl + 2 * y) * W + 2 * x;
+        const long ps[4] = {p00, p00 + 1, p00 + W, p00 + W + 1};
+        if (c < C1) {
+            float s = 0.f;
+            for (int k = 0; k < 4; ++k) s += g[ps[k] * C + c];
+            glow[q * C1 + c] = s;
+        } else {
+            for (int k = 0; k < 4; ++k) gskip[ps[k] * C2 + (c - C1)] = g[ps[k] * C + c];
+        }
+    }
+}
+
+// adjoint of k_pool plus the skip gradient: g[p][c] = glow[parent][c] / 4 + gskip[p][c]
+__global__ void k_pool_bwd_add(const float* __restrict__ glow, const float* __restrict__ gskip, float* __restrict__ g,
+                               long P, int H, int W, int C) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P * C; e += (long)gridDim.x * blockDim.x) {
+        const long p = e / C;
+        const int c = (int)(e % C);
+        const int x = (int)(p % W);
+        const long r = p / W;
+        const int y = (int)(r % H);
+        const long b = r / H;
+        g[e] = 0.25f * glow[((b * (H / 2) + y / 2) * (W / 2) + x / 2) * C + c] + gskip[e];
+    }
+}
+
+// g *= (a > 0): the ReLU derivative from the stored activation
+__global__ void k_relu_mask(float* __restrict__ g, const bf16* __restrict__ a, long n) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+        if (!(__bfloat162float(a[e]) > 0.f)) g[e] = 0.f;
+}
+
+// y[p] = b + sum_c w[c] h[p][c]
+__global__ void k_out_fwd(const bf16* __restrict__ h, const bf16* __restrict__ w, const float* __restrict__ b,
+                          float* __restrict__ y, long P, int C) {
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
+        float s = b[0];
+        for (int c = 0; c < C; ++c) s = fmaf(__bfloat162float(w[c]), __bfloat162float(h[p * C + c]), s);
+        y[p] = s;
+    }
+}
+
+// gy = 2 (y - t) / P; partial[block] = sum (y - t)^2 (FP64)
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, float* __restrict__ gy,
+                      double* __restrict__ partial, long P) {
+    double acc = 0.0;
+    const float sc = 2.0f / (float)P;
+    for (long p = blockIdx.x * (long)blockDim.x + threadIdx.x; p < P; p += (long)gridDim.x * blockDim.x) {
+        const float d = y[p] - t[p];
+        gy[p] = sc * d;
+        acc += (double)d * (double)d;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    }
+}
+
+// output layer backward: gh[p][c] = w[c] gy[p]; gw[c] += sum_p gy[p] h[p][c]; gb += sum_p gy[p]
+// blockDim.x = 256 points, one block per chunk; thread c < C of the block's
+// second phase reduces channel c over the chunk.
+__global__ void k_out_bwd(const float* __restrict__ gy, const bf16* __restrict__ h, const bf16* __restrict__ w,
+                          float* __restrict__ gh, float* __restrict__ gw, float* __restrict__ gb, long P, int C) {
+    const long p0 = blockIdx.x * 256L;
+    for (int e = threadIdx.x; e < 256 * C; e += blockDim.x) {
+        const long p = p0 + e / C;
+        const int c = e % C;
+        if (p < P) gh[p * C + c] = __bfloat162float(w[c]) * gy[p];
+    }
+    for (int c = threadIdx.x; c <= C; c += blockDim.x) {
+        float s = 0.f;
+        for (long p = p0; p < min(P, p0 + 256); ++p) s += (c < C) ? gy[p] * __bfloat162float(h[p * C + c]) : gy[p];
+        atomicAdd(c < C ? &gw[c] : gb, s);
+    }
+}
+
+__global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       bf16* __restrict__ wq, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        const float t = th[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+        th[i] = t;
+        wq[i] = __float2bfloat16_rn(t);
+    }
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ out, long n) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(a[i]);
+}
+
+unsigned grid_for(long n, int threads) {
+    const long b = (n + threads - 1) / threads;
+    return (unsigned)std::max<long>(1, std::min<long>(b, 152L * 32));
+}
+
+}  // namespace
+}  // namespace nsstab
+
+using namespace nsstab;
+
+struct nsstab_unet {
+    int in_ch = 0, width = 0, H = 0, W = 0, lh = 0, lw = 0, maxB = 0;
+    cudaStream_t stream = nullptr;
+    long count = 0;
+    int step = 0;
+    std::vector<ConvDesc> conv;   // 14 convolutions in forward order, then the output layer
+    std::vector<void*> allocs;
+    float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    bf16* wq = nullptr;
+    bf16* x = nullptr;
+    bf16* act[14] = {};           // ReLU outputs of the 14 convolutions
+    bf16* pool[kLevels - 1] = {};
+    bf16* cat[kLevels - 1] = {};  // decoder inputs, by level
+    float* y = nullptr;
+    float* gy = nullptr;
+    float *g0 = nullptr, *g1 = nullptr;   // gradient ping-pong
+    float* gskip[kLevels - 1] = {};
+    float* glow = nullptr;
+    double* partial = nullptr;
+    double* partial_host = nullptr;
+
+    template <class P> int alloc(P** p, size_t count_) {
+        void* q = nullptr;
+        const cudaError_t e = cudaMalloc(&q, std::max<size_t>(count_, 1) * sizeof(P));
+        if (e != cudaSuccess) {
+            set_error(std::string("unet: cudaMalloc: ") + cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? NSSTAB_ERR_OUT_OF_MEMORY : NSSTAB_ERR_CUDA;
+        }
+        allocs.push_back(q);
+        *p = static_cast<P*>(q);
+        return NSSTAB_OK;
+    }
+    ~nsstab_unet() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (void* p : allocs) cudaFree(p);
+        if (partial_host) cudaFreeHost(partial_host);
+    }
+    int c(int l) const { return width << l; }
+    int h(int l) const { return H >> l; }
+    int w(int l) const { return W >> l; }
+};
+
+namespace {
+
+constexpr int kRedBlocksU = 128;
+
+std::vector<ConvDesc> make_layout(int in_ch, int width, long* count) {
+    std::vector<ConvDesc> v;
+    long off = 0;
+    auto add = [&](int ci, int co, int k) {
+        ConvDesc d;
+        d.ci = ci;
+        d.co = co;
+        d.k = k;
+        d.w_off = off;
+        off += (long)co * ci * k * k;
+        d.b_off = off;
+        off += co;
+        v.push_back(d);
+    };
+    int ci = in_ch;
+    for (int l = 0; l < kLevels; ++l) {
+        add(ci, width << l, 3);
+        add(width << l, width << l, 3);
+        ci = width << l;
+    }
+    for (int l = kLevels - 2; l >= 0; --l) {
+        add((width << (l + 1)) + (width << l), width << l, 3);
+        add(width << l, width << l, 3);
+    }
+    add(width, 1, 1);
+    *count = off;
+    return v;
+}
+
+// indices into conv[] / act[]: encoder level l conv s (0 = a, 1 = b) and
+// decoder level l conv s
+int enc_id(int l, int s) { return 2 * l + s; }
+int dec_id(int l, int s) { return 2 * kLevels + 2 * (kLevels - 2 - l) + s; }
+
+int conv_fwd(nsstab_unet* n, int id, const bf16* in, int l, int B) {
+    const ConvDesc& d = n->conv[id];
+    const long P = (long)B * n->h(l) * n->w(l);
+    const dim3 g((unsigned)((P + kFwdThreads - 1) / kFwdThreads), (unsigned)((d.co + kCoTile - 1) / kCoTile));
+    k_conv_fwd<<<g, kFwdThreads, 0, n->stream>>>(in, n->wq + d.w_off, n->theta + d.b_off, n->act[id], P, n->lh - l,
+                                                  n->lw - l, d.ci, d.co);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+// gradient g (of conv id's ReLU output) -> weight/bias gradients and, when
+// gin is not null, the gradient of the conv's input
+int conv_bwd(nsstab_unet* n, int id, const bf16* in, float* g, float* gin, int l, int B) {
+    const ConvDesc& d = n->conv[id];
+    const long P = (long)B * n->h(l) * n->w(l);
+    k_relu_mask<<<grid_for(P * d.co, 256), 256, 0, n->stream>>>(g, n->act[id], P * d.co);
+    NS_LAUNCH_CHECK();
+    const long chunk = std::max<long>(64, (P + 255) / 256);
+    const dim3 gw((unsigned)(((d.co + 15) / 16) * ((d.ci + 15) / 16)), (unsigned)((P + chunk - 1) / chunk));
+    k_conv_bwd_w<<<gw, 256, 0, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P, n->lh - l, n->lw - l,
+                                            d.ci, d.co, chunk);
+    NS_LAUNCH_CHECK();
+    if (gin) {
+        const dim3 gd((unsigned)((P + kFwdThreads - 1) / kFwdThreads), (unsigned)((d.ci + kCoTile - 1) / kCoTile));
+        k_conv_bwd_data<<<gd, kFwdThreads, 0, n->stream>>>(g, n->wq + d.w_off, gin, P, n->lh - l, n->lw - l, d.ci,
+                                                           d.co);
+        NS_LAUNCH_CHECK();
+    }
+    return NSSTAB_OK;
+}
+
+int forward(nsstab_unet* n, const float* x, int B) {
+    const long P0 = (long)B * n->H * n->W;
+    k_to_nhwc<<<grid_for(P0 * n->in_ch, 256), 256, 0, n->stream>>>(x, n->x, P0, n->H * n->W, n->in_ch);
+    NS_LAUNCH_CHECK();
+    const bf16* h = n->x;
+    for (int l = 0; l < kLevels; ++l) {
+        NS_TRY(conv_fwd(n, enc_id(l, 0), h, l, B));
+        NS_TRY(conv_fwd(n, enc_id(l, 1), n->act[enc_id(l, 0)], l, B));
+        h = n->act[enc_id(l, 1)];
+        if (l < kLevels - 1) {
+            const long Po = (long)B * n->h(l + 1) * n->w(l + 1);
+            k_pool<<<grid_for(Po * n->c(l), 256), 256, 0, n->stream>>>(h, n->pool[l], Po, n->h(l + 1), n->w(l + 1),
+                                                                       n->c(l));
+            NS_LAUNCH_CHECK();
+            h = n->pool[l];
+        }
+    }
+    for (int l = kLevels - 2; l >= 0; --l) {
+        const long P = (long)B * n->h(l) * n->w(l);
+        k_up_cat<<<grid_for(P * (n->c(l + 1) + n->c(l)), 256), 256, 0, n->stream>>>(
+            h, n->act[enc_id(l, 1)], n->cat[l], P, n->h(l), n->w(l), n->c(l + 1), n->c(l));
+        NS_LAUNCH_CHECK();
+        NS_TRY(conv_fwd(n, dec_id(l, 0), n->cat[l], l, B));
+        NS_TRY(conv_fwd(n, dec_id(l, 1), n->act[dec_id(l, 0)], l, B));
+        h = n->act[dec_id(l, 1)];
+    }
+    const ConvDesc& o = n->conv.back();
+    k_out_fwd<<<grid_for(P0, 256), 256, 0, n->stream>>>(h, n->wq + o.w_off, n->theta + o.b_off, n->y, P0, n->c(0));
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+int backward(nsstab_unet* n, const float* target, int B, double* loss) {
+    const long P0 = (long)B * n->H * n->W;
+    NS_CUDA(cudaMemsetAsync(n->grad, 0, n->count * sizeof(float), n->stream));
+    k_mse<<<kRedBlocksU, 256, 0, n->stream>>>(n->y, target, n->gy, n->partial, P0);
+    NS_LAUNCH_CHECK();
+    NS_CUDA(cudaMemcpyAsync(n->partial_host, n->partial, kRedBlocksU * sizeof(double), cudaMemcpyDeviceToHost,
+                            n->stream));
+    const ConvDesc& o = n->conv.back();
+    k_out_bwd<<<(unsigned)((P0 + 255) / 256), 256, 0, n->stream>>>(n->gy, n->act[dec_id(0, 1)], n->wq + o.w_off, n->g0,
+                                                                   n->grad + o.w_off, n->grad + o.b_off, P0, n->c(0));
+    NS_LAUNCH_CHECK();
+    float* g = n->g0;      // gradient of the current layer's output
+    float* t = n->g1;      // its input's gradient
+    for (int l = 0; l < kLevels - 1; ++l) {
+        NS_TRY(conv_bwd(n, dec_id(l, 1), n->act[dec_id(l, 0)], g, t, l, B));
+        std::swap(g, t);
+        NS_TRY(conv_bwd(n, dec_id(l, 0), n->cat[l], g, t, l, B));
+        std::swap(g, t);
+        // g: gradient of cat[l]; split into the level below and the skip
+        const long Pl = (long)B * n->h(l + 1) * n->w(l + 1);
+        k_up_cat_bwd<<<grid_for(Pl * (n->c(l + 1) + n->c(l)), 256), 256, 0, n->stream>>>(
+            g, n->glow, n->gskip[l], Pl, n->h(l + 1), n->w(l + 1), n->c(l + 1), n->c(l));
+        NS_LAUNCH_CHECK();
+        const long Pn = Pl * n->c(l + 1);
+        NS_CUDA(cudaMemcpyAsync(g, n->glow, Pn * sizeof(float), cudaMemcpyDeviceToDevice, n->stream));
+    }
+    for (int l = kLevels - 1; l >= 0; --l) {
+        if (l < kLevels - 1) {
+            const long P = (long)B * n->h(l) * n->w(l);
+            k_pool_bwd_add<<<grid_for(P * n->c(l), 256), 256, 0, n->stream>>>(g, n->gskip[l], t, P, n->h(l), n->w(l),
+                                                                              n->c(l));
+            NS_LAUNCH_CHECK();
+            std::swap(g, t);
+        }
+        NS_TRY(conv_bwd(n, enc_id(l, 1), n->act[enc_id(l, 0)], g, t, l, B));
+        std::swap(g, t);
+        const bf16* in = (l == 0) ? n->x : n->pool[l - 1];
+        NS_TRY(conv_bwd(n, enc_id(l, 0), in, g, l == 0 ? nullptr : t, l, B));
+        std::swap(g, t);
+    }
+    NS_CUDA(cudaStreamSynchronize(n->stream));
+    double s = 0.0;
+    for (int b = 0; b < kRedBlocksU; ++b) s += n->partial_host[b];
+    *loss = s / (double)P0;
+    return NSSTAB_OK;
+}
+
+int check_batch(nsstab_unet* n, int B, const void* a, const void* b) {
+    if (!n || !a || !b) {
+        set_error("unet: null argument");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    if (B < 1 || B > n->maxB) {
+        set_error("unet: batch must be in [1, max_batch]");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    return NSSTAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+long unet_param_count(int in_ch, int width) {
+    if (in_ch < 1 || width < 1) return -1;
+    long c = 0;
+    make_layout(in_ch, width, &c);
+    return c;
+}
+
+int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* stream, nsstab_unet** out) {
+    if (!out) {
+        set_error("unet_create: null argument");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    const int q = 1 << (kLevels - 1);
+    if (in_ch < 1 || in_ch > 64 || width < 1 || width > 256 || max_batch < 1 || ny < q || nx < q ||
+        !is_pow2(ny) || !is_pow2(nx) || (long)ny * nx * max_batch > (1L << 28)) {
+        set_error("unet_create: need 1 <= in_ch <= 64, 1 <= width <= 256, max_batch >= 1, ny and nx powers of two "
+                  ">= 8, max_batch*ny*nx <= 2^28");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    nsstab_unet* n = new nsstab_unet();
+    n->in_ch = in_ch;
+    n->width = width;
+    n->H = ny;
+    n->W = nx;
+    n->lh = ilog2(ny);
+    n->lw = ilog2(nx);
+    n->maxB = max_batch;
+    n->stream = (cudaStream_t)stream;
+    n->conv = make_layout(in_ch, width, &n->count);
+    const long B = max_batch;
+    int rc = NSSTAB_OK;
+    auto A = [&](int r) {
+        if (rc == NSSTAB_OK) rc = r;
+    };
+    A(n->alloc(&n->theta, n->count));
+    A(n->alloc(&n->grad, n->count));
+    A(n->alloc(&n->m, n->count));
+    A(n->alloc(&n->v, n->count));
+    A(n->alloc(&n->wq, n->count));
+    A(n->alloc(&n->x, B * ny * nx * in_ch));
+    for (int l = 0; l < kLevels; ++l) {
+        const long P = B * n->h(l) * n->w(l);
+        A(n->alloc(&n->act[enc_id(l, 0)], P * n->c(l)));
+        A(n->alloc(&n->act[enc_id(l, 1)], P * n->c(l)));
+        if (l < kLevels - 1) {
+            A(n->alloc(&n->act[dec_id(l, 0)], P * n->c(l)));
+            A(n->alloc(&n->act[dec_id(l, 1)], P * n->c(l)));
+            A(n->alloc(&n->pool[l], B * n->h(l + 1) * n->w(l + 1) * n->c(l)));
+            A(n->alloc(&n->cat[l], P * (n->c(l + 1) + n->c(l))));
+            A(n->alloc(&n->gskip[l], P * n->c(l)));
+        }
+    }
+    long gmax = 0;
+    for (int l = 0; l < kLevels; ++l) {
+        const long P = B * n->h(l) * n->w(l);
+        gmax = std::max(gmax, P * (n->c(l) + (l + 1 < kLevels ? n->c(l + 1) : 0)));
+        gmax = std::max(gmax, P * (long)(l == 0 ? std::max(in_ch, n->c(0)) : n->c(l - 1)));
+    }
+    A(n->alloc(&n->g0, gmax));
+    A(n->alloc(&n->g1, gmax));
+    A(n->alloc(&n->glow, gmax));
+    A(n->alloc(&n->y, B * ny * nx));
+    A(n->alloc(&n->gy, B * ny * nx));
+    A(n->alloc(&n->partial, kRedBlocksU));
+    if (rc == NSSTAB_OK && cudaMallocHost((void**)&n->partial_host, kRedBlocksU * sizeof(double)) != cudaSuccess) {
+        set_error("unet_create: cudaMallocHost failed");
+        rc = NSSTAB_ERR_OUT_OF_MEMORY;
+    }
+    for (void* z : {(void*)n->theta, (void*)n->m, (void*)n->v})
+        if (rc == NSSTAB_OK && cudaMemsetAsync(z, 0, n->count * sizeof(float), n->stream) != cudaSuccess)
+            rc = NSSTAB_ERR_CUDA;
+    if (rc == NSSTAB_OK && cudaMemsetAsync(n->wq, 0, n->count * sizeof(bf16), n->stream) != cudaSuccess)
+        rc = NSSTAB_ERR_CUDA;
+    if (rc != NSSTAB_OK) {
+        delete n;
+        return rc;
+    }
+    *out = n;
+    return NSSTAB_OK;
+}
+
+void unet_destroy(nsstab_unet* net) { delete net; }
+
+int unet_set_params(nsstab_unet* net, const float* theta) {
+    if (!net || !theta) {
+        set_error("unet_set_params: null argument");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    NS_CUDA(cudaMemcpyAsync(net->theta, theta, net->count * sizeof(float), cudaMemcpyDeviceToDevice, net->stream));
+    NS_CUDA(cudaMemsetAsync(net->m, 0, net->count * sizeof(float), net->stream));
+    NS_CUDA(cudaMemsetAsync(net->v, 0, net->count * sizeof(float), net->stream));
+    net->step = 0;
+    k_to_bf16<<<grid_for(net->count, 256), 256, 0, net->stream>>>(net->theta, net->wq, net->count);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+int unet_get_params(nsstab_unet* net, float* theta) {
+    if (!net || !theta) {
+        set_error("unet_get_params: null argument");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    NS_CUDA(cudaMemcpyAsync(theta, net->theta, net->count * sizeof(float), cudaMemcpyDeviceToDevice, net->stream));
+    return NSSTAB_OK;
+}
+
+int unet_forward(nsstab_unet* net, const float* x, int batch, float* y) {
+    NS_TRY(check_batch(net, batch, x, y));
+    NS_TRY(forward(net, x, batch));
+    NS_CUDA(cudaMemcpyAsync(y, net->y, (size_t)batch * net->H * net->W * sizeof(float), cudaMemcpyDeviceToDevice,
+                            net->stream));
+    return NSSTAB_OK;
+}
+
+int unet_gradient(nsstab_unet* net, const float* x, const float* target, int batch, float* grad, double* loss) {
+    NS_TRY(check_batch(net, batch, x, target));
+    if (!grad || !loss) {
+        set_error("unet_gradient: null argument");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    NS_TRY(forward(net, x, batch));
+    NS_TRY(backward(net, target, batch, loss));
+    NS_CUDA(cudaMemcpyAsync(grad, net->grad, net->count * sizeof(float), cudaMemcpyDeviceToDevice, net->stream));
+    NS_CUDA(cudaStreamSynchronize(net->stream));
+    return NSSTAB_OK;
+}
+
+int unet_train_step(nsstab_unet* net, const float* x, const float* target, int batch, float lr, float beta1,
+                    float beta2, float eps, double* loss) {
+    NS_TRY(check_batch(net, batch, x, target));
+    if (!loss || !(lr > 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0)) {
+        set_error("unet_train_step: need loss != NULL, lr > 0, 0 <= beta < 1, eps > 0");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    NS_TRY(forward(net, x, batch));
+    NS_TRY(backward(net, target, batch, loss));
+    net->step += 1;
+    const float c1 = 1.f - std::pow(beta1, (float)net->step), c2 = 1.f - std::pow(beta2, (float)net->step);
+    k_adam<<<grid_for(net->count, 256), 256, 0, net->stream>>>(net->theta, net->grad, net->m, net->v, net->wq,
+                                                               net->count, lr, beta1, beta2, eps, c1, c2);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+"""Learned initial guess for the Newton-Krylov base-flow solve.
+
+The Newton-Krylov fixed-point method (Sec. 3.1.2, Eq. 43) needs fewer
+iterations the closer its start is to the steady state.  The paper starts
+from a flow field at hand; here a U-Net (the library's `unet_*` calls)
+predicts the base-flow vorticity from the flow parameters, and Newton starts
+from that prediction.
+
+Pipeline (all GPU work in the library; this module draws the seeded inputs,
+moves tensors and keeps the books):
+  1. training labels: base flows for seeded (Re, D) pairs by Newton, in
+     order of Re, each started from the previous converged flow (parameter
+     continuation; the first, and any continuation that fails, from the
+     plain start);
+  2. train the network on (features, label) pairs with Adam;
+  3. for held-out (Re, D): Newton from the network's prediction against
+     Newton from the plain start -- selective frequency damping (Sec. 3.1.1,
+     Eq. 40) from rest for a fixed number of steps -- in iterations,
+     Jacobian products and seconds.
+
+Run as ``python -m paper_1804_03859_gb300.learned_guess [options]``; prints
+one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+
+from . import nsstab
+
+FEATURES = 3
+
+
+def features(nx: int, ny: int, Re: float, D: float, Lx: float = 16.0, Ly: float = 8.0,
+             cyl_x: float = 4.0, cyl_y: float = 4.0) -> np.ndarray:
+    """Network input [3][ny][nx]: a Gaussian bump of radius D/2 at the
+    cylinder (periodic distance), the Reynolds number and the diameter as
+    constant planes, each scaled to order one."""
+    x = np.arange(nx) * (Lx / nx)
+    y = np.arange(ny) * (Ly / ny)
+    ddx = (x - cyl_x + 0.5 * Lx) % Lx - 0.5 * Lx
+    ddy = (y - cyl_y + 0.5 * Ly) % Ly - 0.5 * Ly
+    r2 = ddx[None, :] ** 2 + ddy[:, None] ** 2
+    bump = np.exp(-r2 / (0.5 * D) ** 2)
+    return np.stack([bump, np.full((ny, nx), (Re - 80.0) / 40.0), np.full((ny, nx), (D - 1.0) / 0.2)])
+
+
+def he_init(in_ch: int, width: int, seed: int) -> np.ndarray:
+    """Seeded initial parameters in the library's flat layout: weights
+    normal with variance 2 / fan-in, biases zero."""
+    rng = np.random.default_rng(seed)
+    c = [width << l for l in range(4)]
+    shapes = []
+    ci = in_ch
+    for l in range(4):
+        shapes += [(c[l], ci, 9), (c[l], c[l], 9)]
+        ci = c[l]
+    for l in (2, 1, 0):
+        shapes += [(c[l], c[l + 1] + c[l], 9), (c[l], c[l], 9)]
+    shapes.append((1, c[0], 1))
+    out = []
+    for co, cin, k in shapes:
+        out.append(rng.standard_normal(co * cin * k) * math.sqrt(2.0 / (cin * k)))
+        out.append(np.zeros(co))
+    theta = np.concatenate(out).astype(np.float32)
+    assert theta.size == nsstab.load_library().unet_param_count(in_ch, width)
+    return theta
+
+
+def _solve(st, q, args):
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, r, it, mv = st.newton_krylov_fixedpoint(q, T=args.T, gmres_m=args.gmres_m, tol=args.tol,
+                                                max_newton=args.max_newton)
+    torch.cuda.synchronize()
+    return {"ok": rc == nsstab.OK, "residual": r, "iters": it, "matvecs": mv, "seconds": time.perf_counter() - t0}
+
+
+def plain_start(st, args):
+    """SFD from rest for args.sfd_steps steps (the start without a model)."""
+    import torch
+
+    q = torch.zeros(args.ny, args.nx, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.sfd_baseflow(q, chi=args.chi, Delta=args.Delta, tol=0.0, max_steps=args.sfd_steps,
+                    check_every=args.sfd_steps)
+    torch.cuda.synchronize()
+    return q, time.perf_counter() - t0
+
+
+def sample_params(n: int, seed: int):
+    rng = np.random.default_rng(seed)
+    return [(float(rng.uniform(40.0, 120.0)), float(rng.uniform(0.8, 1.2))) for _ in range(n)]
+
+
+def run(args) -> dict:
+    import torch
+
+    dt = args.dt if args.dt > 0 else 0.01 * 128 / args.nx
+    kw = dict(nx=args.nx, ny=args.ny, dt=dt)
+    t_all = time.perf_counter()
+
+    # 1. dataset: training labels by continuation in Re, test pairs from the plain start
+    def from_plain(Re, D):
+        st = nsstab.Stepper(Re=Re, cyl_D=D, **kw)
+        q, t_sfd = plain_start(st, args)
+        rec = _solve(st, q, args)
+        rec.update(Re=Re, D=D, sfd_seconds=t_sfd, label=q.clone())
+        return rec
+
+    t0 = time.perf_counter()
+    train, prev = [], None
+    for Re, D in sorted(sample_params(args.train, args.seed)):
+        rec = None
+        if prev is not None:
+            st = nsstab.Stepper(Re=Re, cyl_D=D, **kw)
+            q = prev.clone()
+            rec = _solve(st, q, args)
+            rec.update(Re=Re, D=D, label=q.clone())
+            del st
+        if rec is None or not rec["ok"]:
+            rec = from_plain(Re, D)
+        if rec["ok"]:
+            train.append(rec)
+            prev = rec["label"]
+    test = [from_plain(Re, D) for Re, D in sample_params(args.test, args.seed + 1)]
+    t_data = time.perf_counter() - t0
+    if not train:
+        return {"error": "no training base flow converged"}
+
+    # 2. training
+    X = torch.from_numpy(np.stack([features(args.nx, args.ny, r["Re"], r["D"]) for r in train]).astype(np.float32))
+    Y = torch.stack([r["label"] for r in train]).to(torch.float32)
+    scale = float(Y.abs().max())
+    X, Y = X.cuda(), (Y / scale).cuda().contiguous()
+    net = nsstab.UNet(FEATURES, args.width, args.ny, args.nx, max_batch=args.batch)
+    net.unet_set_params(torch.from_numpy(he_init(FEATURES, args.width, args.seed)).cuda())
+    rng = np.random.default_rng(args.seed + 2)
+    B = min(args.batch, len(train))
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(args.iters):
+        idx = torch.from_numpy(rng.choice(len(train), B, replace=False)).cuda()
+        lr = args.lr * (0.05 + 0.95 * 0.5 * (1 + math.cos(math.pi * k / max(1, args.iters))))
+        losses.append(net.unet_train_step(X[idx].contiguous(), Y[idx].contiguous(), lr=lr))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+
+    # 3. held-out pairs: Newton from the prediction vs from the plain start
+    out_rows = []
+    for r in test:
+        st = nsstab.Stepper(Re=r["Re"], cyl_D=r["D"], **kw)
+        x = torch.from_numpy(features(args.nx, args.ny, r["Re"], r["D"])[None].astype(np.float32)).cuda()
+        y = torch.empty(1, args.ny, args.nx, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        net.unet_forward(x, y)
+        q = (y[0].to(torch.float64) * scale).contiguous()
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        guess_err = float(torch.linalg.norm(q - r["label"]) / torch.linalg.norm(r["label"])) if r["ok"] else None
+        rec = _solve(st, q, args)
+        out_rows.append({"Re": r["Re"], "D": r["D"],
+                         "plain": {k: r[k] for k in ("ok", "iters", "matvecs", "seconds", "sfd_seconds")},
+                         "learned": dict(rec, inference_seconds=t_inf, guess_rel_err=guess_err)})
+        del st
+
+    def stat(key, sub):
+        v = [row[key][sub] for row in out_rows if row["plain"]["ok"] and row["learned"]["ok"]]
+        return float(np.mean(v)) if v else None
+
+    return {
+        "workload": f"learned Newton start, {args.nx}x{args.ny}, Re U[40,120], D U[0.8,1.2]",
+        "grid": [args.nx, args.ny], "dt": dt, "T": args.T, "gmres_m": args.gmres_m, "tol": args.tol,
+        "sfd_start": {"steps": args.sfd_steps, "chi": args.chi, "Delta": args.Delta},
+        "train_samples": len(train), "train_requested": args.train, "test_samples": len(test),
+        "unet": {"width": args.width, "params": net.count, "iters": args.iters, "batch": B, "lr": args.lr,
+                 "loss_first": losses[0] if losses else None, "loss_last": float(np.mean(losses[-20:])) if losses else None,
+                 "train_seconds": t_train, "storage": "bf16 activations, fp32 sums"},
+        "data_seconds": t_data,
+        "newton_iters_mean": {"plain": stat("plain", "iters"), "learned": stat("learned", "iters")},
+        "matvecs_mean": {"plain": stat("plain", "matvecs"), "learned": stat("learned", "matvecs")},
+        "newton_seconds_mean": {"plain": stat("plain", "seconds"), "learned": stat("learned", "seconds")},
+        "converged": {"plain": int(sum(r["plain"]["ok"] for r in out_rows)),
+                      "learned": int(sum(r["learned"]["ok"] for r in out_rows))},
+        "guess_rel_err_mean": float(np.mean([r["learned"]["guess_rel_err"] for r in out_rows
+                                            if r["learned"]["guess_rel_err"] is not None] or [np.nan])),
+        "rows": out_rows,
+        "total_seconds": time.perf_counter() - t_all,
+    }
+
+
+def parse(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--ny", type=int, default=64)
+    ap.add_argument("--dt", type=float, default=0.0, help="time step (default 0.01 * 128 / nx)")
+    ap.add_argument("--train", type=int, default=200)
+    ap.add_argument("--test", type=int, default=16)
+    ap.add_argument("--width", type=int, default=24)
+    ap.add_argument("--iters", type=int, default=1500)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--T", type=float, default=0.4)
+    ap.add_argument("--gmres-m", dest="gmres_m", type=int, default=50)
+    ap.add_argument("--tol", type=float, default=1e-10)
+    ap.add_argument("--max-newton", dest="max_newton", type=int, default=30)
+    ap.add_argument("--sfd-steps", dest="sfd_steps", type=int, default=300)
+    ap.add_argument("--chi", type=float, default=0.1)
+    ap.add_argument("--Delta", type=float, default=0.5)
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args(argv)
+
+
+def main(argv=None):
+    from . import build
+
+    build.build()
+    res = run(parse(argv))
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

@@ -99,6 +99,17 @@ SIGNATURES = [
     ("serve_eigs", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(EigJob), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                   ctypes.c_int, ctypes.POINTER(EigJobResult), _ip]),
+    ("unet_param_count", ctypes.c_long, [ctypes.c_int, ctypes.c_int]),
+    ("unet_create", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]),
+    ("unet_destroy", None, [ctypes.c_void_p]),
+    ("unet_set_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("unet_get_params", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("unet_forward", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("unet_gradient", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                     ctypes.c_void_p, _dp]),
+    ("unet_train_step", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                       ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, _dp]),
     ("cgs2_orthogonalize", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
                                           ctypes.c_void_p, _dp, _dp, ctypes.c_void_p]),
     ("cgs2_orthogonalize_noalloc", ctypes.c_int, [ctypes.c_void_p, ctypes.c_long, ctypes.c_long, ctypes.c_int,
@@ -284,6 +295,71 @@ def serve_eigs(jobs, m: int, nev: int, tol: float, T: float, max_restarts: int =
                     "residual": np.array(r.resid[:k]), "n_conv": r.n_conv, "n_matvec": r.n_matvec,
                     "group": r.group, "latency_s": r.latency_s})
     return rc, res, ng.value
+
+
+def _f32_ptr(t, numel, name):
+    import torch
+
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.float32 \
+            or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} values")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class UNet:
+    """Owner of a ``nsstab_unet*`` (the learned base-flow initial guess)."""
+
+    def __init__(self, in_ch: int, width: int, ny: int, nx: int, max_batch: int):
+        self._lib = load_library()
+        self.in_ch, self.width, self.ny, self.nx, self.max_batch = in_ch, width, ny, nx, max_batch
+        self.count = int(self._lib.unet_param_count(in_ch, width))
+        h = ctypes.c_void_p()
+        _check(self._lib.unet_create(in_ch, width, ny, nx, max_batch, current_stream_handle(), ctypes.byref(h)),
+               "unet_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _batch(self, x):
+        B = x.numel() // (self.in_ch * self.ny * self.nx)
+        return B, _f32_ptr(x, B * self.in_ch * self.ny * self.nx, "x")
+
+    def unet_set_params(self, theta):
+        _check(self._lib.unet_set_params(self._h, _f32_ptr(theta, self.count, "theta")), "unet_set_params")
+
+    def unet_get_params(self, theta):
+        _check(self._lib.unet_get_params(self._h, _f32_ptr(theta, self.count, "theta")), "unet_get_params")
+
+    def unet_forward(self, x, y):
+        B, xp = self._batch(x)
+        _check(self._lib.unet_forward(self._h, xp, B, _f32_ptr(y, B * self.ny * self.nx, "y")), "unet_forward")
+
+    def unet_gradient(self, x, target, grad) -> float:
+        B, xp = self._batch(x)
+        loss = ctypes.c_double()
+        _check(self._lib.unet_gradient(self._h, xp, _f32_ptr(target, B * self.ny * self.nx, "target"), B,
+                                       _f32_ptr(grad, self.count, "grad"), ctypes.byref(loss)), "unet_gradient")
+        return loss.value
+
+    def unet_train_step(self, x, target, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                        eps: float = 1e-8) -> float:
+        B, xp = self._batch(x)
+        loss = ctypes.c_double()
+        _check(self._lib.unet_train_step(self._h, xp, _f32_ptr(target, B * self.ny * self.nx, "target"), B,
+                                         float(lr), float(beta1), float(beta2), float(eps), ctypes.byref(loss)),
+               "unet_train_step")
+        return loss.value
 
 
 @dataclass
