@@ -450,6 +450,7 @@ def run_native(args, rank: int, world: int):
     serving = None
     if not args.no_serve and not args.no_eigs:
         serving = serve_leg(args, dev)
+    unet_leg = None if args.no_serve else unet_train_leg(args, dev)
 
     if rank != 0:
         return
@@ -486,8 +487,42 @@ def run_native(args, rank: int, world: int):
         "time_to_eigs": eigs,
         "batched": batched,
         "serving": serving,
+        "unet": unet_leg,
     }
     print(json.dumps(out))
+
+
+def unet_train_leg(args, dev):
+    """Training-step throughput of the learned-initial-guess network
+    (128x64, 3 input planes, width 24, batch 16), CUDA events on its stream."""
+    import torch
+
+    from paper_1804_03859_gb300 import learned_guess, nsstab
+
+    ny, nx, B, width = 64, 128, 16, 24
+    net = nsstab.UNet(learned_guess.FEATURES, width, ny, nx, max_batch=B)
+    net.unet_set_params(torch.from_numpy(learned_guess.he_init(learned_guess.FEATURES, width, 0)).to(dev))
+    rng = np.random.default_rng(7)
+    x = torch.from_numpy(rng.standard_normal((B, learned_guess.FEATURES, ny, nx)).astype(np.float32)).to(dev)
+    t = torch.from_numpy(rng.standard_normal((B, ny, nx)).astype(np.float32)).to(dev)
+    for _ in range(3):
+        net.unet_train_step(x, t, lr=1e-4)
+    n = 20
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(n):
+        net.unet_train_step(x, t, lr=1e-4)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    fl = learned_guess.train_step_flops(learned_guess.FEATURES, width, ny, nx, B)
+    fp32 = N_SMS * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA peak at the maximum SM clock
+    return {"grid": [nx, ny], "batch": B, "width": width, "params": net.count, "ms_per_train_step": ms,
+            "flops_per_step": fl, "tflops": fl / (ms * 1e-3) / 1e12, "fp32_fma_peak_tflops": fp32,
+            "frac_of_fp32_peak": fl / (ms * 1e-3) / 1e12 / fp32,
+            "kernels": "direct FP32-FMA convolutions on bf16 activations (not tensor cores)"}
 
 
 SERVE_JOBS = 24

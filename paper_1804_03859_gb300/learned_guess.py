@@ -71,6 +71,26 @@ def he_init(in_ch: int, width: int, seed: int) -> np.ndarray:
     return theta
 
 
+def train_step_flops(in_ch: int, width: int, ny: int, nx: int, batch: int) -> int:
+    """Multiply-add flops of one training step: every 3x3 convolution's
+    forward, input-gradient and weight-gradient products (2 P Ci Co 9 each;
+    the first layer's input gradient is not formed) and the output layer's
+    three products."""
+    c = [width << l for l in range(4)]
+    convs = []          # (level, ci, co)
+    ci = in_ch
+    for l in range(4):
+        convs += [(l, ci, c[l]), (l, c[l], c[l])]
+        ci = c[l]
+    for l in (2, 1, 0):
+        convs += [(l, c[l + 1] + c[l], c[l]), (l, c[l], c[l])]
+    total = 0
+    for k, (l, cin, co) in enumerate(convs):
+        P = batch * (ny >> l) * (nx >> l)
+        total += 2 * P * cin * co * 9 * (2 if k == 0 else 3)
+    return total + 3 * 2 * batch * ny * nx * c[0]
+
+
 def _solve(st, q, args):
     import torch
 
