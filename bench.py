@@ -558,6 +558,7 @@ def serve_leg(args, dev):
     return {"solves": SERVE_JOBS, "grids": mix, "Re": [40.0, 120.0], "cyl_D": [0.8, 1.2], "precision": "f32",
             "krylov_m": SERVE_M, "nev": SERVE_NEV, "max_restarts": SERVE_RESTARTS, "tol": TOL32, "T": T_SAMPLE,
             "groups": ngroups, "status": rc, "matvecs": int(sum(r["n_matvec"] for r in res)),
+            "error": nsstab.load_library().nsstab_last_error().decode() if rc < 0 else None,
             "converged": int(sum(r["status"] == nsstab.OK for r in res)),
             "wall_seconds": wall, "solves_per_s": SERVE_JOBS / wall,
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
+#include <exception>
 #include <map>
 #include <mutex>
 #include <string>
@@ -79,13 +80,20 @@ static int run_unit(const nsstab_config& base_cfg, const Unit& u, const nsstab_e
     c.Re = Re[0];
     c.cyl_D = D[0];
     cudaStream_t s = nullptr;
-    NS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    StepperBase* st = make_stepper(c, k, Re.data(), D.data(), 1, s);
-    int rc = st->init();
+    StepperBase* st = nullptr;
     std::vector<ArnoldiOut> outs(k);
-    if (rc == NSSTAB_OK) rc = st->set_base_ptrs(base.data());
-    if (rc == NSSTAB_OK)
-        rc = arnoldi_batch_run(st, s, (long)u.nx * u.ny, v0.data(), m, nev, tol, max_restarts, nsteps, outs);
+    int rc = NSSTAB_OK;
+    const cudaError_t es = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (es != cudaSuccess) {
+        set_error(std::string("serve_eigs: cudaStreamCreateWithFlags: ") + cudaGetErrorString(es));
+        rc = NSSTAB_ERR_CUDA;
+    } else {
+        st = make_stepper(c, k, Re.data(), D.data(), 1, s);
+        rc = st->init();
+        if (rc == NSSTAB_OK) rc = st->set_base_ptrs(base.data());
+        if (rc == NSSTAB_OK)
+            rc = arnoldi_batch_run(st, s, (long)u.nx * u.ny, v0.data(), m, nev, tol, max_restarts, nsteps, outs);
+    }
     const double t_end = steady_seconds();
     for (int i = 0; i < k; ++i) {
         nsstab_eig_result& r = results[u.jobs[i]];
@@ -108,7 +116,7 @@ static int run_unit(const nsstab_config& base_cfg, const Unit& u, const nsstab_e
         }
     }
     delete st;   // synchronises the stream and frees the stepper's memory
-    cudaStreamDestroy(s);
+    if (s) cudaStreamDestroy(s);
     return rc;
 }
 
@@ -116,9 +124,29 @@ static int run_unit(const nsstab_config& base_cfg, const Unit& u, const nsstab_e
 
 using namespace nsstab;
 
+static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+                           double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
+                           nsstab_eig_result* results, int* ngroups);
+
+// No C++ exception (thread creation, host allocation) crosses the C ABI.
 extern "C" int serve_eigs(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
                           double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
                           nsstab_eig_result* results, int* ngroups) {
+    try {
+        return serve_eigs_impl(cfg, njobs, jobs, m, nev, tol, max_restarts, T, mem_budget, max_concurrent, results,
+                               ngroups);
+    } catch (const std::exception& e) {
+        set_error(std::string("serve_eigs: ") + e.what());
+        return NSSTAB_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        set_error("serve_eigs: unexpected host exception");
+        return NSSTAB_ERR_CUDA;
+    }
+}
+
+static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+                           double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
+                           nsstab_eig_result* results, int* ngroups) {
     auto bad = [](const std::string& msg) {
         set_error(msg);
         return NSSTAB_ERR_INVALID_ARG;
@@ -225,7 +253,14 @@ extern "C" int serve_eigs(const nsstab_config* cfg, int njobs, const nsstab_eig_
                 sh.used += units[pick].bytes;
             }
             const Unit& u = units[pick];
-            const int rc = run_unit(*cfg, u, jobs, m, nev, tol, max_restarts, nsteps[u.jobs[0]], t0, results);
+            int rc;
+            try {   // an exception must not end a worker thread (std::terminate)
+                rc = run_unit(*cfg, u, jobs, m, nev, tol, max_restarts, nsteps[u.jobs[0]], t0, results);
+            } catch (...) {
+                set_error("serve_eigs: host exception while running a group");
+                rc = NSSTAB_ERR_OUT_OF_MEMORY;
+                for (int i : u.jobs) results[i].status = rc;
+            }
             {
                 std::lock_guard<std::mutex> lk(sh.mu);
                 sh.used -= u.bytes;

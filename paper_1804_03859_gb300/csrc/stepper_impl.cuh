@@ -823,8 +823,17 @@ template <class T> Launch StepperImpl<T>::default_plan(int kid) const {
     return L;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel function,
+// shared by every stepper in the process: each one raises it to the same
+// library-wide cap (never to its own plan's size), so steppers on other
+// grids running concurrently in other threads can never lower it below
+// what their launches need.  A launch still requests only L.smem.
 template <class T> int StepperImpl<T>::set_smem_attr(int kid, const Launch& L) {
-    const int sm = (int)L.smem;
+    if (L.smem > kMaxSmem) {
+        set_error("launch plan needs more shared memory than the library allows");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    const int sm = (int)kMaxSmem;
 #define NS_ATTR(fn) NS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm))
 #define NS_ATTR_LE(KERNEL)                 \
     switch (L.le) {                        \

@@ -99,6 +99,19 @@ def test_budget_below_one_solve_fails_those_solves(jobs):
     assert all(r["status"] == -3 for r in res)
 
 
+def test_double_float_serving_batch(jobs, alone):
+    rc, res, _ = nsstab.serve_eigs(jobs, m=M, nev=NEV, tol=TOL, T=T, max_restarts=60, precision=48)
+    assert rc == nsstab.OK
+    for r, mu in zip(res, alone):
+        assert _match(r["mu"], mu) <= 1e-8
+
+
+def test_one_job_and_a_single_group(jobs, alone):
+    rc, res, ngroups = nsstab.serve_eigs(jobs[3:4], m=M, nev=NEV, tol=TOL, T=T, max_restarts=60)
+    assert rc == nsstab.OK and ngroups == 1 and res[0]["group"] == 0
+    assert _match(res[0]["mu"], alone[3]) <= 1e-8
+
+
 def test_fp32_serving_batch(jobs, alone):
     """FP32 steppers in the serving batch: leading values within 1e-5 relative."""
     rc, res, _ = nsstab.serve_eigs(jobs, m=M, nev=NEV, tol=1e-6, T=T, max_restarts=60, precision=32)
@@ -106,3 +119,20 @@ def test_fp32_serving_batch(jobs, alone):
     for r, mu in zip(res, alone):
         for x in r["mu"]:
             assert np.min(np.abs(mu - x)) <= 1e-5 * abs(x)
+
+
+def test_concurrent_groups_on_four_grids_raise_no_error():
+    """Groups on grids with different launch plans run at once in separate
+    threads (launch attributes are shared per kernel function)."""
+    jobs = []
+    for i, (nx, ny) in enumerate([(32, 16), (64, 32), (128, 64), (256, 128)] * 3):
+        dt = 0.01 * 128 / nx
+        jobs.append(dict(nx=nx, ny=ny, dt=dt, Re=50.0 + i, cyl_D=1.0,
+                         base=_dev(inputs.wake_like_field(ny, nx, seed=80 + i)),
+                         v0=_dev(inputs.gaussian_field(ny, nx, seed=90 + i))))
+    for _ in range(3):
+        rc, res, ngroups = nsstab.serve_eigs(jobs, m=24, nev=2, tol=1e-6, T=0.32, max_restarts=2, precision=32,
+                                             max_concurrent=4)
+        assert rc >= 0, nsstab.load_library().nsstab_last_error()
+        assert ngroups == 4
+        assert all(r["status"] >= 0 and r["n_matvec"] > 0 for r in res)
