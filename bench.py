@@ -400,6 +400,26 @@ def run_native(args, rank: int, world: int):
                 errs = [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in r.mu]
                 d["rel_err_vs_fp64"] = errs
             eigs[f"fp{prec}"] = d
+        # the same eigenproblem with a block of 2 vectors per product with M
+        # and twice the basis (block Krylov-Schur; the batched stepper runs
+        # the 2 products at once)
+        for prec in (64, 48):
+            stb2 = nsstab.Stepper(per_set=2, nx=NX, ny=NY, dt=DT, Re=RE, precision=prec)
+            if not args.no_tune:
+                stb2.stepper_autotune(reps=3)
+            v2 = torch.from_numpy(np.stack([inputs.gaussian_field(NY, NX, seed=400 + i) for i in range(2)])).to(dev)
+            v2[0].copy_(v0)
+            stb2.stepper_set_base(base)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = stb2.block_arnoldi_eigs(None, v2, m=2 * KRYLOV_M, nev=NEV, tol=1e-8, T=T_SAMPLE, max_restarts=8)
+            el = time.perf_counter() - t0
+            d = {"seconds": el, "n_matvec": r.n_matvec, "n_conv": r.n_conv, "n_eig": len(r.mu), "tol": 1e-8,
+                 "block": 2, "krylov_m": 2 * KRYLOV_M, "leading_mu": [r.mu[0].real, r.mu[0].imag]}
+            if ref_mu is not None:
+                d["rel_err_vs_fp64"] = [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in r.mu]
+            eigs[f"fp{prec}_block2"] = d
+            del stb2
 
     # batched: 16 Reynolds numbers in 40..100 (one base flow each) stepped in
     # one launch per kernel, FP32 stepper, and their 16 eigenproblems solved

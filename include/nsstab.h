@@ -249,6 +249,29 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
                        double* eig_re, double* eig_im, double* resid, double* eigvecs,
                        int* n_eig, int* n_conv, int* n_matvec);
 
+/* Block Krylov-Schur: ONE eigenproblem of M = exp(T A) about the base flow,
+ * built with a block of b vectors per product with M, so that every product
+ * is one batched run of the step kernels over b fields (b times the
+ * parallelism of arnoldi_eigs on the same grid).  Each new basis column is
+ * orthogonalised by CGS2 against every column before it (Algorithm 1's
+ * Gram-Schmidt step); the projected matrix is then banded with b
+ * sub-diagonals, and the residual of a Ritz pair (mu, V y) is ||R y|| with
+ * R the b rows below its square part.  The restart keeps the wanted Schur
+ * vectors and the b residual columns (Sec. 3.2.2 with a rank-b instead of a
+ * rank-1 remainder).  The paper's Algorithm 1 is the case b = 1.
+ *   st:   a batch with ONE parameter set and b = per_set members
+ *         (batch_create(cfg, 1, Re, D, b, ...)); b = 1 is a plain stepper
+ *   base_omega: device [ny][nx] or NULL (current base)
+ *   v0:   device [b][ny][nx], the start block (linearly independent)
+ *   m:    basis size, 2 (nev + 1) + 2 b <= m <= 1024
+ *   other arguments and outputs: as arnoldi_eigs (n_matvec counts single
+ *   products, b per round).
+ * Allocates about (2 m + 4 b) n doubles during the call.  Synchronous. */
+int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
+                       int m, int nev, double tol, int max_restarts, double T,
+                       double* eig_re, double* eig_im, double* resid, double* eigvecs,
+                       int* n_eig, int* n_conv, int* n_matvec);
+
 /* ------------------------------------------------------------------------
  * Serving batch: many independent eigen-solves on mixed grids.
  *

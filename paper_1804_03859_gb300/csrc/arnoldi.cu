@@ -301,4 +301,181 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
     return NSSTAB_OK;
 }
 
+// Block Krylov-Schur for ONE eigenproblem with a block of b = members
+// vectors per product with M (the batched stepper's members share one base
+// flow).  Column c of the basis is orthogonalised by CGS2 against all
+// columns before it, so M V_j = V_{j+b} B with B banded (b sub-diagonals);
+// the residual of a Ritz pair (theta, V y) is ||R y||, R the b rows of B
+// below the square part.  The restart keeps the wanted Schur vectors and
+// the b residual columns: M V_p = V_p T_p + V_res (R Z_p), the block form
+// of Sec. 3.2.2's decomposition (Eqs. 60-63 have b = 1).
+int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
+                      double tol, int max_restarts, int nsteps, ArnoldiOut& out) {
+    const double delta = 0.05;
+    const int b = st->members();
+    const int ncol = m + 2 * b;      // basis columns held
+    const int ldb = m + 2 * b;       // rows of the projected matrix
+    DevBuf Vd, tmp, Cd;
+    NS_CUDA(cudaMalloc(&Vd.p, (size_t)n * ncol * sizeof(double)));
+    NS_CUDA(cudaMalloc(&Cd.p, (size_t)ncol * ncol * sizeof(double)));
+    NS_CUDA(cudaMalloc(&tmp.p, (size_t)n * ncol * sizeof(double)));
+    double* V = Vd.p;
+    GsWork gs;
+    struct Release {
+        GsWork& g;
+        ~Release() { g.release(); }
+    } rel{gs};
+    std::vector<double> h(ncol), B((size_t)ldb * (m + b), 0.0);
+    // orthonormal start block
+    for (int i = 0; i < b; ++i) {
+        double* w = V + (size_t)i * n;
+        NS_CUDA(cudaMemcpyAsync(w, v0[i], n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+        double nrm = 0.0, beta = 0.0;
+        NS_TRY(vec_norm(w, n, &nrm, gs, stream));
+        NS_TRY(cgs2(V, n, n, i, w, h.data(), &beta, gs, stream));
+        if (!(nrm > 0.0) || !std::isfinite(nrm) || !(beta > 1e-10 * nrm)) {
+            set_error("block_arnoldi_eigs: start vectors are zero, non-finite or linearly dependent");
+            return NSSTAB_ERR_INVALID_ARG;
+        }
+        NS_TRY(vec_scale(w, w, n, 1.0 / beta, stream));
+    }
+    std::vector<const double*> in(b);
+    std::vector<double*> outp(b);
+    std::vector<double> T, Z;
+    std::vector<dense::cd> ev;
+    std::vector<int> order;
+    std::vector<double> res;
+    int j = 0, mm = 0, k = 0, conv = 0, restarts = 0, matvec = 0;
+    while (true) {
+        for (int i = 0; i < b; ++i) {
+            in[i] = V + (size_t)(j + i) * n;
+            outp[i] = V + (size_t)(j + b + i) * n;
+        }
+        NS_TRY(st->step_linear_ptrs(in.data(), outp.data(), nsteps));
+        matvec += b;
+        bool breakdown = false;
+        for (int i = 0; i < b; ++i) {
+            const int c = j + b + i, col = j + i;
+            double beta = 0.0;
+            NS_TRY(cgs2(V, n, n, c, V + (size_t)c * n, h.data(), &beta, gs, stream));
+            double hn = 0.0;
+            for (int r = 0; r < c; ++r) {
+                B[r + (size_t)col * ldb] = h[r];
+                hn += h[r] * h[r];
+            }
+            B[c + (size_t)col * ldb] = beta;
+            if (!std::isfinite(beta)) {
+                set_error("block_arnoldi_eigs: non-finite values in the Krylov basis");
+                return NSSTAB_DIVERGED;
+            }
+            if (beta <= 1e-14 * std::max(1.0, std::sqrt(hn))) {
+                breakdown = true;   // invariant subspace: the factorisation is exact
+                B[c + (size_t)col * ldb] = 0.0;
+            } else {
+                NS_TRY(vec_scale(V + (size_t)c * n, V + (size_t)c * n, n, 1.0 / beta, stream));
+            }
+        }
+        j += b;
+        if (j < m && !breakdown) continue;
+        // full factorisation of order mm: Schur form, Ritz values, residuals ||R y||
+        mm = j;
+        T.assign((size_t)mm * mm, 0.0);
+        Z.assign((size_t)mm * mm, 0.0);
+        for (int c = 0; c < mm; ++c) {
+            Z[c + (size_t)c * mm] = 1.0;
+            for (int r = 0; r < mm; ++r) T[r + (size_t)c * mm] = B[r + (size_t)c * ldb];
+        }
+        dense::hessenberg(mm, T.data(), Z.data());
+        if (dense::schur(mm, T.data(), Z.data()) != 0) {
+            set_error("block_arnoldi_eigs: QR iteration on the projected matrix did not converge");
+            return NSSTAB_ERR_NUMERICAL;
+        }
+        ev = dense::schur_eigenvalues(mm, T.data());
+        order = leading_order(ev);
+        k = take_leading(ev, order, nev);
+        res.assign(k, 0.0);
+        conv = 0;
+        for (int s2 = 0; s2 < k; ++s2) {
+            const std::vector<dense::cd> y = ritz_vector(mm, T.data(), Z.data(), ev, order[s2]);
+            double r2 = 0.0;
+            for (int q = 0; q < b; ++q) {
+                dense::cd acc = 0.0;
+                for (int c = 0; c < mm; ++c) acc += B[(mm + q) + (size_t)c * ldb] * y[c];
+                r2 += std::norm(acc);
+            }
+            res[s2] = std::sqrt(r2);
+            if (res[s2] <= tol) ++conv;
+        }
+        if (conv >= k || restarts >= max_restarts || breakdown) break;
+        // restart: keep p Schur vectors and the b residual columns.  A block
+        // basis of mm columns holds only mm / b powers of M, so keeping just
+        // the values with |mu| >= 1 - delta (the single-vector rule) can
+        // leave too small a space to converge a clustered spectrum (seen to
+        // stall); keep at least half of the basis beyond the k wanted.
+        int p = 0;
+        for (const auto& e : ev)
+            if (std::abs(e) >= 1.0 - delta) ++p;
+        p = std::max(k, std::min(std::max(p, k + (mm - k) / 2), mm - b));
+        std::vector<double> mags(mm);
+        for (int s2 = 0; s2 < mm; ++s2) mags[s2] = std::abs(ev[s2]);
+        std::sort(mags.begin(), mags.end(), std::greater<double>());
+        const double thr = mags[p - 1] * (1.0 - 1e-12);
+        const int psel =
+            dense::schur_reorder(mm, T.data(), Z.data(), [&](dense::cd e) { return std::abs(e) >= thr; });
+        if (psel <= 0 || psel + b > mm) {
+            set_error("block_arnoldi_eigs: Schur reordering failed");
+            return NSSTAB_ERR_NUMERICAL;
+        }
+        p = psel;
+        NS_CUDA(cudaMemcpyAsync(Cd.p, Z.data(), (size_t)mm * p * sizeof(double), cudaMemcpyHostToDevice, stream));
+        NS_TRY(basis_combine(V, n, n, mm, Cd.p, p, tmp.p, n, stream));
+        NS_CUDA(cudaMemcpyAsync(V, tmp.p, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+        NS_CUDA(cudaMemcpyAsync(V + (size_t)p * n, V + (size_t)mm * n, (size_t)n * b * sizeof(double),
+                                cudaMemcpyDeviceToDevice, stream));
+        std::vector<double> Bn((size_t)ldb * (m + b), 0.0);
+        for (int c = 0; c < p; ++c) {
+            for (int r = 0; r < p; ++r) Bn[r + (size_t)c * ldb] = T[r + (size_t)c * mm];
+            for (int q = 0; q < b; ++q) {
+                double acc = 0.0;
+                for (int r = 0; r < mm; ++r) acc += B[(mm + q) + (size_t)r * ldb] * Z[r + (size_t)c * mm];
+                Bn[(p + q) + (size_t)c * ldb] = acc;
+            }
+        }
+        B.swap(Bn);
+        NS_CUDA(cudaStreamSynchronize(stream));   // Z upload done before Cd is reused
+        j = p;
+        ++restarts;
+    }
+    out.n_eig = k;
+    out.n_conv = conv;
+    out.n_matvec = matvec;
+    out.restarts = restarts;
+    out.mu.resize(k);
+    out.resid = res;
+    for (int s2 = 0; s2 < k; ++s2) out.mu[s2] = ev[order[s2]];
+    out.status = (conv >= k) ? NSSTAB_OK : NSSTAB_NOT_CONVERGED;
+    out.done_at = steady_seconds();
+    if (out.eigvecs) {
+        std::vector<double> Y((size_t)mm * k, 0.0);
+        int s2 = 0;
+        while (s2 < k) {
+            const std::vector<dense::cd> y = ritz_vector(mm, T.data(), Z.data(), ev, order[s2]);
+            if (ev[order[s2]].imag() != 0.0 && s2 + 1 < k) {
+                for (int r = 0; r < mm; ++r) {
+                    Y[r + (size_t)s2 * mm] = y[r].real();
+                    Y[r + (size_t)(s2 + 1) * mm] = y[r].imag();
+                }
+                s2 += 2;
+            } else {
+                for (int r = 0; r < mm; ++r) Y[r + (size_t)s2 * mm] = y[r].real();
+                s2 += 1;
+            }
+        }
+        NS_CUDA(cudaMemcpyAsync(Cd.p, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
+        NS_TRY(basis_combine(V, n, n, mm, Cd.p, k, out.eigvecs, n, stream));
+    }
+    NS_CUDA(cudaStreamSynchronize(stream));
+    return NSSTAB_OK;
+}
+
 }  // namespace nsstab

@@ -27,4 +27,11 @@ double steady_seconds();
 int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
                       double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs);
 
+// One eigenproblem solved with a block of b = st->members() vectors per
+// product with M (block Krylov-Schur); the members must share one base flow
+// (one parameter set).  v0: host array of b device pointers (the start
+// block, linearly independent).  Requires m >= 2 (nev + 1) + 2 b.
+int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
+                      double tol, int max_restarts, int nsteps, ArnoldiOut& out);
+
 }  // namespace nsstab

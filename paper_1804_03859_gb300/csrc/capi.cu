@@ -252,6 +252,44 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
     return status;
 }
 
+int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0, int m, int nev, double tol,
+                       int max_restarts, double T, double* eig_re, double* eig_im, double* resid, double* eigvecs,
+                       int* n_eig, int* n_conv, int* n_matvec) {
+    if (!st || !v0 || !eig_re || !eig_im || !resid || !n_eig || !n_conv || !n_matvec)
+        return bad_arg("block_arnoldi_eigs: null argument");
+    if (st->impl->sets() != 1) return bad_arg("block_arnoldi_eigs: the stepper must have one parameter set");
+    const int b = st->impl->members();
+    const long n = (long)st->cfg.nx * st->cfg.ny;
+    if (nev < 1) return bad_arg("block_arnoldi_eigs: need nev >= 1");
+    if (m > 1024 || m + 2L * b >= n || m < 2 * (nev + 1) + 2 * b)
+        return bad_arg("block_arnoldi_eigs: need 2 (nev + 1) + 2 b <= m <= 1024 and m + 2 b < nx*ny");
+    if (max_restarts < 0) return bad_arg("block_arnoldi_eigs: max_restarts < 0");
+    if (!(tol >= 0)) return bad_arg("block_arnoldi_eigs: tol < 0");
+    int nsteps = 0;
+    NS_TRY(steps_for(st->cfg, T, &nsteps));
+    if (base_omega) {
+        NS_TRY(st->impl->set_base(base_omega));
+        st->have_base = true;
+    } else if (!st->have_base) {
+        return bad_arg("block_arnoldi_eigs: no base flow (pass base_omega or call stepper_set_base)");
+    }
+    std::vector<const double*> v0p(b);
+    for (int i = 0; i < b; ++i) v0p[i] = v0 + (size_t)i * n;
+    ArnoldiOut out;
+    out.eigvecs = eigvecs;
+    const int rc = block_arnoldi_run(st->impl, st->stream, n, v0p.data(), m, nev, tol, max_restarts, nsteps, out);
+    if (rc < 0) return rc;
+    for (int s = 0; s < out.n_eig; ++s) {
+        eig_re[s] = out.mu[s].real();
+        eig_im[s] = out.mu[s].imag();
+        resid[s] = out.resid[s];
+    }
+    *n_eig = out.n_eig;
+    *n_conv = out.n_conv;
+    *n_matvec = out.n_matvec;
+    return rc != NSSTAB_OK ? rc : out.status;
+}
+
 int newton_krylov_fixedpoint_ex(nsstab_stepper* st, nsstab_stepper* lin_st, double* omega, double T, int gmres_m,
                                 double gmres_rtol, int gmres_restarts, double tol, int max_newton, double* residual,
                                 int* newton_iters, int* matvecs) {

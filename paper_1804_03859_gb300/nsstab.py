@@ -96,6 +96,9 @@ SIGNATURES = [
     ("stepper_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     ("stepper_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("stepper_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, _ip]),
+    ("block_arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                          _dp, ctypes.c_void_p, _ip, _ip, _ip]),
     ("serve_eigs", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(EigJob), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                   ctypes.c_int, ctypes.POINTER(EigJobResult), _ip]),
@@ -518,6 +521,27 @@ class Stepper:
                                            im.ctypes.data_as(_dp), res.ctypes.data_as(_dp), ev,
                                            ctypes.byref(n_eig), ctypes.byref(n_conv), ctypes.byref(n_mv)),
                     "arnoldi_eigs", allow_soft=True)
+        k = n_eig.value
+        return EigResult(re[:k] + 1j * im[:k], res[:k], n_conv.value, n_mv.value, rc)
+
+    def block_arnoldi_eigs(self, base, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
+                           eigvecs=None) -> EigResult:
+        """One eigenproblem with a block of ``members`` vectors per product
+        with M (a stepper made as ``Stepper(per_set=b, Re=scalar, ...)``);
+        v0: [b, ny, nx] start block."""
+        re, im, res = np.zeros(nev + 1), np.zeros(nev + 1), np.zeros(nev + 1)
+        n_eig, n_conv, n_mv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        bp = self._p(base, "base", 1) if base is not None else None
+        ev = None
+        if eigvecs is not None:
+            if eigvecs.shape[0] < nev + 1:
+                raise ValueError("eigvecs must hold nev + 1 fields")
+            ev = _field_ptr(eigvecs, self.shape, "eigvecs")
+        rc = _check(self._lib.block_arnoldi_eigs(self._h, bp, self._p(v0, "v0"), int(m), int(nev), float(tol),
+                                                 int(max_restarts), float(T), re.ctypes.data_as(_dp),
+                                                 im.ctypes.data_as(_dp), res.ctypes.data_as(_dp), ev,
+                                                 ctypes.byref(n_eig), ctypes.byref(n_conv), ctypes.byref(n_mv)),
+                    "block_arnoldi_eigs", allow_soft=True)
         k = n_eig.value
         return EigResult(re[:k] + 1j * im[:k], res[:k], n_conv.value, n_mv.value, rc)
 

@@ -157,6 +157,55 @@ def test_fp32_eigenvalues_track_fp64_on_a_fine_grid():
         assert np.min(np.abs(ref.mu - mu)) <= 1e-5 * abs(mu)
 
 
+@pytest.mark.parametrize("b", [1, 2, 4])
+def test_block_krylov_schur_matches_dense_eigendecomposition(small, b):
+    kw, cfg, base, T, mu_dense = small
+    st = nsstab.Stepper(per_set=b, **kw)
+    v0 = np.stack([inputs.gaussian_field(16, 32, seed=40 + i) for i in range(b)])
+    res = st.block_arnoldi_eigs(_dev(base), _dev(v0), m=60, nev=4, tol=1e-10, T=T, max_restarts=200)
+    assert res.status == nsstab.OK and res.n_conv == len(res.mu)
+    assert _match(res.mu, mu_dense[:6]) <= 1e-10
+    assert res.n_matvec % b == 0
+
+
+def test_block_krylov_schur_matches_single_vector_on_a_wake():
+    kw = dict(nx=128, ny=64, dt=0.01, Re=50.0)
+    cfg = ns2d.Config(**kw)
+    base = _dev(ns2d.step_nonlinear(np.zeros((64, 128)), 300, cfg))
+    T = 0.5
+    v0 = np.stack([inputs.gaussian_field(64, 128, seed=50 + i) for i in range(4)])
+    one = nsstab.Stepper(**kw).arnoldi_eigs(base, _dev(v0[0]), m=64, nev=6, tol=1e-9, T=T, max_restarts=40)
+    blk = nsstab.Stepper(per_set=2, **kw).block_arnoldi_eigs(base, _dev(v0[:2]), m=128, nev=6, tol=1e-9, T=T,
+                                                             max_restarts=60)
+    assert one.n_conv == len(one.mu) and blk.n_conv == len(blk.mu)
+    assert _match(blk.mu, one.mu) <= 1e-8 and _match(one.mu, blk.mu) <= 1e-8
+    ev = torch.empty(7, 64, 128, dtype=torch.float64, device="cuda")
+    st = nsstab.Stepper(per_set=2, **kw)
+    r2 = st.block_arnoldi_eigs(base, _dev(v0[:2]), m=64, nev=2, tol=1e-9, T=T, max_restarts=40, eigvecs=ev)
+    # leading Ritz vector: M x = mu x to the Ritz residual (a complex pair is
+    # stored as Re in slot 0 and Im in slot 1, and M Re = Re(mu) Re - Im(mu) Im)
+    x = ev[0].clone()
+    mx = torch.empty_like(x)
+    nsstab.Stepper(**kw).apply_expTL(base, x, mx, T)
+    mu = r2.mu[0]
+    ref = mu.real * x - (mu.imag * ev[1] if mu.imag != 0 else 0.0)
+    assert float(torch.linalg.norm(mx - ref)) <= 1e-7
+
+
+def test_block_krylov_schur_rejects_bad_input():
+    kw = dict(nx=32, ny=16, dt=0.02, Re=50.0)
+    base = _dev(np.zeros((16, 32)))
+    st = nsstab.Stepper(per_set=2, **kw)
+    same = _dev(np.stack([inputs.gaussian_field(16, 32, seed=1)] * 2))
+    with pytest.raises(nsstab.NsstabError):
+        st.block_arnoldi_eigs(base, same, m=40, nev=2, tol=1e-8, T=0.4)     # dependent start block
+    with pytest.raises(nsstab.NsstabError):
+        st.block_arnoldi_eigs(base, same, m=8, nev=2, tol=1e-8, T=0.4)      # m too small for b and nev
+    two_sets = nsstab.Stepper(Re=[40.0, 50.0], nx=32, ny=16, dt=0.02)
+    with pytest.raises(nsstab.NsstabError):
+        two_sets.block_arnoldi_eigs(None, same, m=40, nev=2, tol=1e-8, T=0.4)
+
+
 def test_invalid_krylov_arguments():
     st = nsstab.Stepper(nx=16, ny=8)
     v0 = _dev(inputs.gaussian_field(8, 16, seed=1))
