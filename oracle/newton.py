@@ -5,9 +5,12 @@ Newton iteration of Sec. 3.1.2 (Eq. 43): x_{k+1} = x_k - (I - M)^{-1}
 is left to a Krylov method; here restarted GMRES with CGS2 Arnoldi
 (Algorithm 1) and Givens rotations, the projected least-squares problem
 solved by back substitution.  For the Navier-Stokes map G = Phi_T (T/dt
-steps of the nonlinear stepper) the product with M is the linearised march
-about the current iterate (frozen base flow), which equals the exact Jacobian
-at a steady state and differs from it by O(||x - G(x)||) near one.
+steps of the nonlinear stepper) the product with M is, by default, the exact
+discrete tangent (ns2d.apply_tangent: the linearised step about each point
+of the trajectory, advanced together with it); jacobian="frozen" instead
+marches the linearised equations about the current iterate, which equals
+the exact Jacobian at a steady state and differs from it by O(||x - G(x)||)
+near one.
 """
 from __future__ import annotations
 
@@ -112,11 +115,14 @@ def newton_krylov(G, jac_matvec, residual, x0, tol: float, max_newton: int, m: i
 
 
 def newton_baseflow(cfg: ns2d.Config, omega0, T: float, tol: float, max_newton: int, m: int = 50,
-                    gmres_rtol: float = 1e-3, max_restarts: int = 2) -> NewtonResult:
+                    gmres_rtol: float = 1e-3, max_restarts: int = 2, jacobian: str = "tangent") -> NewtonResult:
     """Steady base flow: fixed point of Phi_T (T/dt nonlinear steps), stopped on
     the residual r(q) = ||G_1(q) - q||_h / dt."""
     nT = ns2d.steps_per_period(T, cfg)
     G = lambda q: ns2d.step_nonlinear(q, nT, cfg)
-    J = lambda q, v: ns2d.apply_expTL(ns2d.Base.from_omega(q, cfg), v, T, cfg)
+    if jacobian == "tangent":
+        J = lambda q, v: ns2d.apply_tangent(q, v, T, cfg)
+    else:
+        J = lambda q, v: ns2d.apply_expTL(ns2d.Base.from_omega(q, cfg), v, T, cfg)
     return newton_krylov(G, J, lambda q: ns2d.residual(q, cfg), omega0, tol, max_newton, m, gmres_rtol,
                          max_restarts)

@@ -266,6 +266,25 @@ def step_linear(v0, nsteps: int, base: Base, cfg: Config):
     return v
 
 
+def apply_tangent(q, v, T: float, cfg: Config):
+    """Exact discrete tangent of the nonlinear map Phi_T (T/dt steps, AB1
+    start) at q, applied to v: dPhi_T(q)/dq v.  The perturbation is advanced
+    together with the trajectory (co-integration): step n linearises about
+    the trajectory point q_n, and its AB2 history term is the linearised
+    advection of step n-1 about q_{n-1}, which is the derivative of the
+    two-step scheme itself.  The Newton-Krylov Jacobian of Sec. 3.1.2
+    (Eq. 43) is I - apply_tangent."""
+    nsteps = steps_per_period(T, cfg)
+    w = np.array(q, dtype=np.float64, copy=True)
+    dv = np.array(v, dtype=np.float64, copy=True)
+    Nw = Nv = None
+    for k in range(nsteps):
+        base = Base.from_omega(w, cfg)
+        dv, Nv = step(dv, Nv, cfg, first=(k == 0), base=base)
+        w, Nw = step(w, Nw, cfg, first=(k == 0))
+    return dv
+
+
 def steps_per_period(T: float, cfg: Config) -> int:
     ns = T / cfg.dt
     k = int(round(ns))

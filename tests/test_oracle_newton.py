@@ -54,3 +54,17 @@ def test_newton_base_flow_matches_sfd_and_meets_the_residual_target():
                                        check_every=200)
     assert ok
     assert np.abs(res.x - X).max() <= 1e-8 * np.abs(X).max()
+
+
+def test_exact_tangent_and_frozen_jacobian_reach_the_same_fixed_point():
+    """The default Newton Jacobian is the co-integrated tangent; the frozen
+    linearisation reaches the same fixed point (it is exact there) but
+    needs at least as many iterations from a start far from it."""
+    cfg = ns2d.Config(nx=32, ny=16, dt=0.02, Re=40.0)
+    q0 = ns2d.step_nonlinear(np.zeros((16, 32)), 20, cfg)
+    a = newton.newton_baseflow(cfg, q0, T=0.4, tol=1e-10, max_newton=30, m=40, gmres_rtol=1e-8)
+    b = newton.newton_baseflow(cfg, q0, T=0.4, tol=1e-10, max_newton=30, m=40, gmres_rtol=1e-8,
+                               jacobian="frozen")
+    assert a.converged and b.converged
+    assert np.abs(a.x - b.x).max() <= 1e-8 * np.abs(a.x).max()
+    assert a.iters <= b.iters

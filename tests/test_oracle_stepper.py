@@ -116,6 +116,29 @@ def test_tangent_is_exact_derivative_of_quadratic_step():
     assert np.linalg.norm((gp - g0) / 1e-2 - jv) > 1e-6 * np.linalg.norm(jv)
 
 
+def test_co_integrated_tangent_is_the_derivative_of_phi_T():
+    """apply_tangent against central differences of the oracle's own
+    nonlinear map over 10 steps: the error falls like eps^2, and the
+    linearisation frozen at q (a different operator away from a fixed point)
+    is far outside that error."""
+    cfg = ns2d.Config(nx=64, ny=32, dt=0.02, Re=50.0)
+    q = inputs.wake_like_field(32, 64, seed=5)
+    v = inputs.smooth_field(32, 64, seed=6)
+    T = 10 * cfg.dt
+    jv = ns2d.apply_tangent(q, v, T, cfg)
+    errs = []
+    for eps in (1e-2, 1e-3):
+        fd = (ns2d.step_nonlinear(q + eps * v, 10, cfg) - ns2d.step_nonlinear(q - eps * v, 10, cfg)) / (2 * eps)
+        errs.append(np.linalg.norm(fd - jv) / np.linalg.norm(jv))
+    assert errs[1] <= 1e-6 and 50 < errs[0] / errs[1] < 150, errs
+    frozen = ns2d.apply_expTL(ns2d.Base.from_omega(q, cfg), v, T, cfg)
+    assert np.linalg.norm(frozen - jv) / np.linalg.norm(jv) > 1e3 * errs[1]
+    # one step: the tangent is the single linearised step about q
+    one = ns2d.apply_tangent(q, v, cfg.dt, cfg)
+    assert np.allclose(one, ns2d.step(v, None, cfg, first=True, base=ns2d.Base.from_omega(q, cfg))[0],
+                       rtol=0, atol=1e-14 * np.abs(one).max())
+
+
 def test_mean_free_and_mirror_symmetric_wake():
     """Impulsive start past a cylinder on the box's mid-line: the vorticity stays
     mean-free and antisymmetric, omega(x, Ly - y) = -omega(x, y)."""
