@@ -135,27 +135,48 @@ int sfd_baseflow(nsstab_stepper* st, double* omega, double chi, double Delta,
 
 /* Steady base flow by Newton-Krylov (Sec. 3.1.2, Eq. 43): iterate
  *   q <- q - (I - M)^{-1} (q - Phi_T(q)),
- * Phi_T = T/dt nonlinear steps (AB1 start), M = exp(T A) about the current
- * iterate, the linear system solved by GMRES(gmres_m) with CGS2 to the
- * relative residual 1e-3 (at most 2 restarts), until the base-flow residual
- * r(q) of stepper_residual is <= tol or max_newton Newton steps were made.
- * Unlike SFD it also converges to unstable steady states with real
- * (non-oscillating) unstable eigenvalues.  omega: device [ny][nx], in:
- * initial guess, out: last iterate.  *residual (r of the last iterate),
- * *newton_iters, *matvecs (products with M): host.  Allocates
- * n (gmres_m + 5) doubles during the call.  Single steppers only.  Returns
- * NSSTAB_OK, NSSTAB_NOT_CONVERGED or NSSTAB_DIVERGED.  Synchronous. */
+ * Phi_T = T/dt nonlinear steps (AB1 start), M = dPhi_T/dq at the current
+ * iterate: the exact discrete tangent (see apply_tangent), the linear system
+ * solved by GMRES(gmres_m) with CGS2 to the relative residual 1e-3 (at
+ * most 2 restarts), until the base-flow residual r(q) of stepper_residual is
+ * <= tol or max_newton Newton steps were made.  Unlike SFD it also
+ * converges to unstable steady states with real (non-oscillating) unstable
+ * eigenvalues.  omega: device [ny][nx], in: initial guess, out: last
+ * iterate.  *residual (r of the last iterate), *newton_iters, *matvecs
+ * (products with M): host.  Allocates n (gmres_m + 5) doubles and a
+ * two-member stepper of st's configuration during the call.  Single
+ * steppers only.  Returns NSSTAB_OK, NSSTAB_NOT_CONVERGED or
+ * NSSTAB_DIVERGED.  Synchronous. */
 int newton_krylov_fixedpoint(nsstab_stepper* st, double* omega, double T, int gmres_m,
                              double tol, int max_newton, double* residual,
                              int* newton_iters, int* matvecs);
 
-/* The same with the Krylov products taken from lin_st (same grid and dt;
- * NULL = st), e.g. an FP32 stepper while st (FP64) evaluates Phi_T and the
- * residual, and with the GMRES relative tolerance and restart count given. */
+/* The same with the Krylov products taken in lin_st's arithmetic (same
+ * grid and dt; NULL = st), e.g. FP32 while st (FP64) evaluates Phi_T and
+ * the residual, with the GMRES relative tolerance and restart count given,
+ * and the Jacobian chosen: jacobian = NSSTAB_JACOBIAN_TANGENT (the exact
+ * discrete tangent, marched by a two-member stepper of lin_st's
+ * configuration made for the call) or NSSTAB_JACOBIAN_FROZEN (lin_st's
+ * linearised propagator about the current iterate: exact only at the fixed
+ * point, one march per product instead of two). */
+#define NSSTAB_JACOBIAN_TANGENT 0
+#define NSSTAB_JACOBIAN_FROZEN 1
 int newton_krylov_fixedpoint_ex(nsstab_stepper* st, nsstab_stepper* lin_st, double* omega,
                                 double T, int gmres_m, double gmres_rtol, int gmres_restarts,
-                                double tol, int max_newton, double* residual,
+                                double tol, int max_newton, int jacobian, double* residual,
                                 int* newton_iters, int* matvecs);
+
+/* Exact discrete tangent of Phi_T (T/dt nonlinear steps, AB1 start) at q,
+ * applied to v_in: v_out = dPhi_T(q)/dq v_in.  Computed by co-integration:
+ * member 0 of st marches q with the nonlinear step while member 1 marches
+ * v with the step linearised about member 0's state of the same step (the
+ * AB2 history term linearised about the previous state), which is the
+ * derivative of the discrete scheme itself, not of the continuous
+ * equations.  st: a batch of two members and one parameter set
+ * (batch_create(cfg, 1, Re, D, 2, ...)); its base fields are overwritten
+ * (set a base again before a frozen-base product).  q, v_in, v_out: device
+ * [ny][nx]; v_out may alias v_in.  Asynchronous. */
+int apply_tangent(nsstab_stepper* st, const double* q, const double* v_in, double* v_out, double T);
 
 /* Leading eigenvalues of M = exp(T A) about base_omega (Sec. 3.2).
  * max_restarts == 0: one m-step Arnoldi factorisation (Algorithm 1) with

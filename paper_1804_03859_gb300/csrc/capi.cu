@@ -290,11 +290,23 @@ int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const doubl
     return rc != NSSTAB_OK ? rc : out.status;
 }
 
+int apply_tangent(nsstab_stepper* st, const double* q, const double* v_in, double* v_out, double T) {
+    if (!st || !q || !v_in || !v_out) return bad_arg("apply_tangent: null argument");
+    if (st->impl->members() != 2 || st->impl->sets() != 1)
+        return bad_arg("apply_tangent: needs a batch of two members and one parameter set");
+    int nsteps = 0;
+    NS_TRY(steps_for(st->cfg, T, &nsteps));
+    st->have_base = false;
+    return st->impl->tangent(q, v_in, v_out, nsteps);
+}
+
 int newton_krylov_fixedpoint_ex(nsstab_stepper* st, nsstab_stepper* lin_st, double* omega, double T, int gmres_m,
-                                double gmres_rtol, int gmres_restarts, double tol, int max_newton, double* residual,
-                                int* newton_iters, int* matvecs) {
+                                double gmres_rtol, int gmres_restarts, double tol, int max_newton, int jacobian,
+                                double* residual, int* newton_iters, int* matvecs) {
     if (!st || !omega || !residual || !newton_iters || !matvecs)
         return bad_arg("newton_krylov_fixedpoint: null argument");
+    if (jacobian != NSSTAB_JACOBIAN_TANGENT && jacobian != NSSTAB_JACOBIAN_FROZEN)
+        return bad_arg("newton_krylov_fixedpoint: jacobian must be NSSTAB_JACOBIAN_TANGENT or _FROZEN");
     nsstab_stepper* lin = lin_st ? lin_st : st;
     if (st->impl->members() != 1 || lin->impl->members() != 1)
         return bad_arg("newton_krylov_fixedpoint: single steppers only");
@@ -306,16 +318,30 @@ int newton_krylov_fixedpoint_ex(nsstab_stepper* st, nsstab_stepper* lin_st, doub
     int nsteps = 0;
     NS_TRY(steps_for(st->cfg, T, &nsteps));
     const long n = (long)st->cfg.nx * st->cfg.ny;
-    const int rc = newton_run(st->impl, lin->impl, st->stream, n, omega, nsteps, gmres_m, gmres_rtol, gmres_restarts,
-                              tol, max_newton, residual, newton_iters, matvecs);
-    lin->have_base = true;
+    StepperBase* tan = nullptr;
+    if (jacobian == NSSTAB_JACOBIAN_TANGENT) {
+        // the two-member stepper of the co-integration, in lin's arithmetic, on st's stream
+        tan = make_stepper(lin->cfg, 1, &lin->cfg.Re, &lin->cfg.cyl_D, 2, st->stream);
+        const int ri = tan->init();
+        if (ri != NSSTAB_OK) {
+            delete tan;
+            return ri;
+        }
+    }
+    const int rc = newton_run(st->impl, lin->impl, tan, st->stream, n, omega, nsteps, gmres_m, gmres_rtol,
+                              gmres_restarts, tol, max_newton, residual, newton_iters, matvecs);
+    if (tan) {
+        delete tan;
+    } else {
+        lin->have_base = true;   // lin now holds the last iterate as its base
+    }
     return rc;
 }
 
 int newton_krylov_fixedpoint(nsstab_stepper* st, double* omega, double T, int gmres_m, double tol, int max_newton,
                              double* residual, int* newton_iters, int* matvecs) {
-    return newton_krylov_fixedpoint_ex(st, nullptr, omega, T, gmres_m, 1e-3, 2, tol, max_newton, residual,
-                                       newton_iters, matvecs);
+    return newton_krylov_fixedpoint_ex(st, nullptr, omega, T, gmres_m, 1e-3, 2, tol, max_newton,
+                                       NSSTAB_JACOBIAN_TANGENT, residual, newton_iters, matvecs);
 }
 
 int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, double* kernel_ms) {

@@ -1,14 +1,18 @@
 // Newton-Krylov fixed-point solver (Sec. 3.1.2, Eq. 43) around the stepper:
 //   q <- q - (I - M)^{-1} (q - Phi_T(q)),
-// Phi_T = T/dt nonlinear steps, M = exp(T A) the linearised propagator about
-// the current iterate (frozen base flow: the exact Jacobian at a steady
-// state, O(||q - Phi_T(q)||) away from it near one).  The linear system is
+// Phi_T = T/dt nonlinear steps, M its Jacobian at q: by default the exact
+// discrete tangent (a two-member stepper advancing the trajectory from q and
+// the perturbation linearised about each of its points, co-integration), or
+// the linearised propagator about q itself (frozen base flow: the exact
+// Jacobian at a steady state, O(||q - Phi_T(q)||) away from it near one,
+// one march per product instead of two).  The linear system is
 // solved by restarted GMRES(m) whose Arnoldi basis is orthogonalised with
 // CGS2 on the GPU; the (m+1) x m least-squares problem is reduced by Givens
 // rotations on the host.  The products with M may come from a second
 // stepper (for instance FP32) while the residual and the nonlinear map use
 // the first (FP64): an inexact Newton method with an FP64 residual.
 #include <cmath>
+#include <functional>
 #include <vector>
 
 #include "newton.h"
@@ -24,8 +28,10 @@ struct DevBuf {
     }
 };
 
+using Product = std::function<int(const double*, double*)>;   // w = M v
+
 // x = GMRES(m) solution of (I - M) x = b from x = 0.
-int gmres_dev(StepperBase* lin, int nsteps, long n, const double* b, double* x, int m, double rtol, int max_restarts,
+int gmres_dev(const Product& Mv, long n, const double* b, double* x, int m, double rtol, int max_restarts,
               double* V, double* r, double* t, double* Cd, GsWork& gs, cudaStream_t stream, int* nmv) {
     double beta0 = 0.0;
     NS_TRY(vec_norm(b, n, &beta0, gs, stream));
@@ -45,7 +51,7 @@ int gmres_dev(StepperBase* lin, int nsteps, long n, const double* b, double* x, 
         for (int j = 0; j < m; ++j) {
             double* vj = V + (size_t)j * n;
             double* w = V + (size_t)(j + 1) * n;
-            NS_TRY(lin->step_linear(vj, w, nsteps));          // w = M v_j
+            NS_TRY(Mv(vj, w));                                 // w = M v_j
             ++*nmv;
             NS_TRY(vec_axpby(w, 1.0, vj, -1.0, w, n, stream));  // w = (I - M) v_j
             double hn = 0.0;
@@ -85,7 +91,7 @@ int gmres_dev(StepperBase* lin, int nsteps, long n, const double* b, double* x, 
         NS_CUDA(cudaStreamSynchronize(stream));   // y staged before it is reused
         if (conv || rs == max_restarts) break;
         // r = b - (I - M) x
-        NS_TRY(lin->step_linear(x, t, nsteps));
+        NS_TRY(Mv(x, t));
         ++*nmv;
         NS_TRY(vec_axpby(t, 1.0, x, -1.0, t, n, stream));
         NS_TRY(vec_axpby(r, 1.0, b, -1.0, t, n, stream));
@@ -95,9 +101,9 @@ int gmres_dev(StepperBase* lin, int nsteps, long n, const double* b, double* x, 
 
 }  // namespace
 
-int newton_run(StepperBase* st, StepperBase* lin, cudaStream_t stream, long n, double* q, int nsteps, int m,
-               double gmres_rtol, int max_restarts, double tol, int max_newton, double* res_out, int* iters_out,
-               int* mv_out) {
+int newton_run(StepperBase* st, StepperBase* lin, StepperBase* tan, cudaStream_t stream, long n, double* q,
+               int nsteps, int m, double gmres_rtol, int max_restarts, double tol, int max_newton, double* res_out,
+               int* iters_out, int* mv_out) {
     DevBuf V, r, x, t, u, Cd;
     NS_CUDA(cudaMalloc(&V.p, (size_t)n * (m + 1) * sizeof(double)));
     NS_CUDA(cudaMalloc(&r.p, n * sizeof(double)));
@@ -129,9 +135,14 @@ int newton_run(StepperBase* st, StepperBase* lin, cudaStream_t stream, long n, d
         NS_CUDA(cudaMemcpyAsync(u.p, q, n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
         NS_TRY(st->step_nonlinear(u.p, nsteps));
         NS_TRY(vec_axpby(r.p, 1.0, q, -1.0, u.p, n, stream));
-        NS_TRY(lin->set_base(q));
-        NS_TRY(gmres_dev(lin, nsteps, n, r.p, x.p, m, gmres_rtol, max_restarts, V.p, u.p, t.p, Cd.p, gs, stream,
-                         &nmv));
+        Product Mv;
+        if (tan) {
+            Mv = [&](const double* v, double* w) { return tan->tangent(q, v, w, nsteps); };
+        } else {
+            NS_TRY(lin->set_base(q));
+            Mv = [&](const double* v, double* w) { return lin->step_linear(v, w, nsteps); };
+        }
+        NS_TRY(gmres_dev(Mv, n, r.p, x.p, m, gmres_rtol, max_restarts, V.p, u.p, t.p, Cd.p, gs, stream, &nmv));
         NS_TRY(vec_axpby(q, 1.0, q, -1.0, x.p, n, stream));
     }
     NS_CUDA(cudaStreamSynchronize(stream));

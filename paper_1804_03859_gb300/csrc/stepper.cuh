@@ -27,6 +27,9 @@ struct StepperBase {
     // per-member device pointers (host arrays of B); a null input pointer
     // leaves that member out of this call
     virtual int step_linear_ptrs(const double* const* in, double* const* out, int nsteps) = 0;
+    // exact discrete tangent of Phi_T (nsteps nonlinear steps) at q applied
+    // to v_in, by co-integration; needs a batch of two members, one set
+    virtual int tangent(const double* q, const double* v_in, double* v_out, int nsteps) = 0;
     virtual int residual(const double* q, double* r) = 0;   // r: host [B]
     virtual int sfd(double* omega, double chi, double Delta, double tol, long max_steps,
                     int check_every, double* r, long* steps) = 0;

@@ -676,6 +676,7 @@ class StepperImpl : public StepperBase {
     int set_base_ptrs(const double* const* base_omegas) override;
     int step_linear(const double* v_in, double* v_out, int nsteps) override;
     int step_linear_ptrs(const double* const* in, double* const* out, int nsteps) override;
+    int tangent(const double* q, const double* v_in, double* v_out, int nsteps) override;
     int residual(const double* q, double* r) override;
     int sfd(double* omega, double chi, double Delta, double tol, long max_steps, int check_every,
             double* r, long* steps) override;
@@ -705,6 +706,8 @@ class StepperImpl : public StepperBase {
     double* red_ = nullptr;          // device partials [B][kRedBlocks]
     double* red_host_ = nullptr;     // pinned
     unsigned char* active_ = nullptr;
+    unsigned char* tmask_ = nullptr;               // device {1, 0, 0, 1}: member 0 alone, member 1 alone
+    const unsigned char* act_override_ = nullptr;  // mask for the next launches (null: the stepper's own)
     std::vector<unsigned char> active_host_;
     const double** ptr_in_ = nullptr;   // device arrays of B member pointers
     double** ptr_out_ = nullptr;
@@ -760,8 +763,10 @@ class StepperImpl : public StepperBase {
     int transform_W();                                   // X1 = x-spectrum of W
     int stream_function(cudaStream_t st);                // Wh, X2 (X3), P (U, V) from X1
     int psi_function(cudaStream_t st);                   // Wh, X2, P from X1
-    int issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last);
-    int run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1 = true);
+    int issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last,
+                    bool tangent = false);
+    int run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1 = true, bool tangent = false);
+    int alloc_base_fields();
     int sumsq_diff(const T* a, const T* b, double* out);   // out[B]
     int time_kernel(int kid, const Launch& L, int reps, float* ms);
 };
@@ -913,20 +918,22 @@ template <class T> int StepperImpl<T>::launch_plain(cudaStream_t st) {
 template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first) {
     const Launch& L = plan_[kid];
     const dim3 g(L.blocks, B_);
+    Fields<T> fl = f_;   // passed by value: a graph capture records this launch's mask
+    if (act_override_) fl.active = act_override_;
     switch (kid) {
         case KCOLP: {
-#define CALL_COLP(le) k_col_poisson<T, le, kF32<T>><<<g, L.threads, L.smem, st>>>(f_, L.per, scale_)
+#define CALL_COLP(le) k_col_poisson<T, le, kF32<T>><<<g, L.threads, L.smem, st>>>(fl, L.per, scale_)
             NS_DISPATCH_LE(L, CALL_COLP);
             break;
         }
         case KINVP: {
-#define CALL_INVP(le) K_INVP(le)<<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper)
+#define CALL_INVP(le) K_INVP(le)<<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper)
             NS_DISPATCH_LE(L, CALL_INVP);
             break;
         }
         case KFWDR: {
-#define CALL_FRL(le) k_row_forward<T, FWD_RHS_LIN, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
-#define CALL_FRN(le) k_row_forward<T, FWD_RHS_NL, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
+#define CALL_FRL(le) k_row_forward<T, FWD_RHS_LIN, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, false, true)
+#define CALL_FRN(le) k_row_forward<T, FWD_RHS_NL, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, false, true)
             if (linear) {
                 NS_DISPATCH_LE(L, CALL_FRL);
             } else {
@@ -936,18 +943,18 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
         }
         case KCOLU: {
             const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
-#define CALL_COLU(le) k_col_update<T, le><<<g, L.threads, L.smem, st>>>(f_, L.per, c1, c0, first)
+#define CALL_COLU(le) k_col_update<T, le><<<g, L.threads, L.smem, st>>>(fl, L.per, c1, c0, first)
             NS_DISPATCH_LE(L, CALL_COLU);
             break;
         }
         case KINVR: {
-#define CALL_INVR(le) K_INVR(le)<<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper)
+#define CALL_INVR(le) K_INVR(le)<<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper)
             NS_DISPATCH_LE(L, CALL_INVR);
             break;
         }
         default: {
-#define CALL_FPL(le) k_row_forward<T, FWD_PEN_LIN, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
-#define CALL_FPN(le) k_row_forward<T, FWD_PEN_NL, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, sfd, do_fft)
+#define CALL_FPL(le) k_row_forward<T, FWD_PEN_LIN, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, sfd, do_fft)
+#define CALL_FPN(le) k_row_forward<T, FWD_PEN_NL, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, sfd, do_fft)
             if (linear) {
                 NS_DISPATCH_LE(L, CALL_FPL);
             } else {
@@ -1244,7 +1251,37 @@ template <class T> int StepperImpl<T>::psi_function(cudaStream_t st) {
 // Enqueue nsteps time steps on `st`.  first_ab1: the first of them is AB1.
 // fft_last: the last step also forms the x-spectrum of its result.
 template <class T>
-int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last) {
+int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool sfd, bool first_ab1, bool fft_last,
+                                bool tangent) {
+    if (tangent) {
+        // co-integration (members: 0 = trajectory, 1 = perturbation): both
+        // streamfunctions, the base fields of the trajectory's current
+        // state, then each row pass in its own mode; the column passes
+        // are the same for both
+        for (int s = 0; s < nsteps; ++s) {
+            const bool first = first_ab1 && s == 0;
+            const bool fft = fft_last || (s + 1 < nsteps);
+            NS_TRY(stream_function(st));
+            k_base_fields<T><<<dim3(kPtBlocks, 1), 256, 0, st>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb,
+                                                                 (T*)f_.DyOb);
+            NS_LAUNCH_CHECK();
+            act_override_ = tmask_;
+            int rc = launch(KFWDR, st, false, false, true, first);
+            act_override_ = tmask_ + 2;
+            if (rc == NSSTAB_OK) rc = launch(KFWDR, st, true, false, true, first);
+            act_override_ = nullptr;
+            NS_TRY(rc);
+            NS_TRY(launch(KCOLU, st, true, false, true, first));
+            NS_TRY(launch(KINVR, st, true, false, true, first));
+            act_override_ = tmask_;
+            rc = launch(KFWDP, st, false, false, fft, first);
+            act_override_ = tmask_ + 2;
+            if (rc == NSSTAB_OK) rc = launch(KFWDP, st, true, false, fft, first);
+            act_override_ = nullptr;
+            NS_TRY(rc);
+        }
+        return NSSTAB_OK;
+    }
     for (int s = 0; s < nsteps; ++s) {
         const bool first = first_ab1 && s == 0;
         NS_TRY(stream_function(st));
@@ -1261,23 +1298,25 @@ int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool s
 // stream and launched into the stepper's stream; the AB2 history carries
 // from one chunk to the next through the workspace.  The active-member mask
 // is read from device memory at run time, so graphs serve any subset.
-template <class T> int StepperImpl<T>::run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1) {
+template <class T>
+int StepperImpl<T>::run_steps(int nsteps, bool linear, bool sfd, bool fft_last, bool first_ab1, bool tangent) {
     if (linear && !have_base_) {
         set_error("linearised step requested before a base flow was set");
         return NSSTAB_ERR_INVALID_ARG;
     }
-    if (nsteps < 4) return issue_steps(stream_, nsteps, linear, sfd, first_ab1, fft_last);
+    if (nsteps < 4) return issue_steps(stream_, nsteps, linear, sfd, first_ab1, fft_last, tangent);
     int done = 0;
     while (done < nsteps) {
         const int len = std::min(kGraphChunk, nsteps - done);
         const bool first = first_ab1 && done == 0;
         const bool last_fft = (done + len < nsteps) || fft_last;
-        const GraphKey key{len, (linear ? 1 : 0) | (sfd ? 2 : 0) | (first ? 4 : 0) | (last_fft ? 8 : 0)};
+        const GraphKey key{len, (linear ? 1 : 0) | (sfd ? 2 : 0) | (first ? 4 : 0) | (last_fft ? 8 : 0) |
+                                    (tangent ? 16 : 0)};
         auto it = graphs_.find(key);
         if (it == graphs_.end()) {
             cudaGraph_t g = nullptr;
             NS_CUDA(cudaStreamBeginCapture(cap_, cudaStreamCaptureModeThreadLocal));
-            const int rc = issue_steps(cap_, len, linear, sfd, first, last_fft);
+            const int rc = issue_steps(cap_, len, linear, sfd, first, last_fft, tangent);
             const cudaError_t ec = cudaStreamEndCapture(cap_, &g);
             if (rc != NSSTAB_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -1409,7 +1448,7 @@ template <class T> int StepperImpl<T>::set_base(const double* base_omega) {
     return set_base_ptrs(p.data());
 }
 
-template <class T> int StepperImpl<T>::set_base_ptrs(const double* const* base_omegas) {
+template <class T> int StepperImpl<T>::alloc_base_fields() {
     if (!f_.Ub) {
         T *Ub, *Vb, *DxOb, *DyOb;
         NS_TRY(dalloc(&Ub, (size_t)S_ * n_));
@@ -1419,6 +1458,11 @@ template <class T> int StepperImpl<T>::set_base_ptrs(const double* const* base_o
         f_.Ub = Ub; f_.Vb = Vb; f_.DxOb = DxOb; f_.DyOb = DyOb;
         clear_graphs();   // captured kernels carry the field pointers by value
     }
+    return NSSTAB_OK;
+}
+
+template <class T> int StepperImpl<T>::set_base_ptrs(const double* const* base_omegas) {
+    NS_TRY(alloc_base_fields());
     // the S base flows go through member slots 0..S-1
     std::vector<unsigned char> a(B_, 0);
     std::vector<const double*> src(B_, nullptr);
@@ -1461,6 +1505,34 @@ template <class T> int StepperImpl<T>::step_linear_ptrs(const double* const* in,
         NS_TRY(run_steps(nsteps, true, false, false));
     }
     return scatter(f_.W, out);
+}
+
+// dPhi_T(q)/dq v_in for the stepper's two members (one parameter set):
+// member 0 marches q nonlinearly, member 1 marches v linearised about
+// member 0's state of the same step (co-integration).  The base fields are
+// overwritten along the way: a later linearised step needs a new base.
+template <class T> int StepperImpl<T>::tangent(const double* q, const double* v_in, double* v_out, int nsteps) {
+    if (B_ != 2 || S_ != 1) {
+        set_error("tangent: needs a batch of two members and one parameter set");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    NS_TRY(alloc_base_fields());
+    if (!tmask_) {
+        NS_TRY(dalloc(&tmask_, 4));
+        const unsigned char m4[4] = {1, 0, 0, 1};
+        NS_CUDA(cudaMemcpy(tmask_, m4, 4, cudaMemcpyHostToDevice));
+        clear_graphs();
+    }
+    have_base_ = false;
+    NS_TRY(all_active());
+    const double* src[2] = {q, v_in};
+    NS_TRY(gather(src));
+    if (nsteps > 0) {
+        NS_TRY(transform_W());
+        NS_TRY(run_steps(nsteps, false, false, false, true, true));
+    }
+    double* dst[2] = {nullptr, v_out};
+    return scatter(f_.W, dst);
 }
 
 template <class T> int StepperImpl<T>::sumsq_diff(const T* a, const T* b, double* out) {

@@ -85,7 +85,9 @@ SIGNATURES = [
                                                 ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]),
     ("newton_krylov_fixedpoint_ex", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                                   ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]),
+                                                   ctypes.c_double, ctypes.c_int, ctypes.c_int, _dp, _ip, _ip]),
+    ("apply_tangent", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_double]),
     ("arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                     ctypes.c_void_p, _ip, _ip, _ip]),
@@ -468,18 +470,29 @@ class Stepper:
                     "sfd_baseflow", allow_soft=True)
         return rc, (float(r[0]) if self.members == 1 else r), steps.value
 
+    JACOBIANS = {"tangent": 0, "frozen": 1}
+
     def newton_krylov_fixedpoint(self, omega, T: float, gmres_m: int, tol: float, max_newton: int,
-                                 lin=None, gmres_rtol: float = 1e-3, gmres_restarts: int = 2):
-        """Newton-Krylov base flow; lin: optional second Stepper for the Jacobian products."""
+                                 lin=None, gmres_rtol: float = 1e-3, gmres_restarts: int = 2,
+                                 jacobian: str = "tangent"):
+        """Newton-Krylov base flow; lin: optional second Stepper whose
+        arithmetic the Jacobian products use; jacobian: "tangent" (exact
+        discrete tangent, co-integrated) or "frozen" (linearised about the
+        current iterate)."""
         r = ctypes.c_double()
         it, mv = ctypes.c_int(), ctypes.c_int()
         rc = _check(self._lib.newton_krylov_fixedpoint_ex(self._h, lin._h if lin is not None else None,
                                                           self._p(omega, "omega"), float(T), int(gmres_m),
                                                           float(gmres_rtol), int(gmres_restarts), float(tol),
-                                                          int(max_newton), ctypes.byref(r), ctypes.byref(it),
-                                                          ctypes.byref(mv)),
+                                                          int(max_newton), self.JACOBIANS[jacobian],
+                                                          ctypes.byref(r), ctypes.byref(it), ctypes.byref(mv)),
                     "newton_krylov_fixedpoint", allow_soft=True)
         return rc, r.value, it.value, mv.value
+
+    def apply_tangent(self, q, v_in, v_out, T: float):
+        """v_out = dPhi_T(q)/dq v_in (a Stepper(per_set=2, ...) of one parameter set)."""
+        _check(self._lib.apply_tangent(self._h, self._p(q, "q", 1), self._p(v_in, "v_in", 1),
+                                       self._p(v_out, "v_out", 1), float(T)), "apply_tangent")
 
     def batch_arnoldi_eigs(self, bases, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
                            eigvecs=None) -> list:
