@@ -471,6 +471,7 @@ def run_native(args, rank: int, world: int):
     if not args.no_serve and not args.no_eigs:
         serving = serve_leg(args, dev)
     unet_leg = None if args.no_serve else unet_train_leg(args, dev)
+    newton_leg = None if (args.no_serve or args.no_eigs) else newton_leg_run(args, dev)
 
     if rank != 0:
         return
@@ -508,8 +509,36 @@ def run_native(args, rank: int, world: int):
         "batched": batched,
         "serving": serving,
         "unet": unet_leg,
+        "newton": newton_leg,
     }
     print(json.dumps(out))
+
+
+def newton_leg_run(args, dev):
+    """Steady base flow of the bench workload (512x256, Re 60) by
+    Newton-Krylov: FP64 nonlinear map and residual, Jacobian products by the
+    exact tangent in FP32 arithmetic (inexact Newton), from 300 steps of
+    selective frequency damping from rest."""
+    import torch
+
+    from paper_1804_03859_gb300 import nsstab
+
+    kw = dict(nx=NX, ny=NY, dt=DT, Re=RE)
+    st = nsstab.Stepper(**kw)
+    lin = nsstab.Stepper(precision=32, **kw)
+    q = torch.zeros(NY, NX, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st.sfd_baseflow(q, chi=0.1, Delta=0.5, tol=0.0, max_steps=300, check_every=300)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    rc, r, it, mv = st.newton_krylov_fixedpoint(q, T=0.4, gmres_m=50, tol=1e-10, max_newton=30, lin=lin)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    return {"workload": f"steady base flow {NX}x{NY}, Re {RE}", "T": 0.4, "gmres_m": 50, "tol": 1e-10,
+            "jacobian": "exact tangent (co-integrated), f32", "start": "300 SFD steps from rest (chi 0.1, Delta 0.5)",
+            "status": rc, "residual": r, "newton_iters": it, "jacobian_products": mv, "sfd_seconds": t1 - t0,
+            "newton_seconds": t2 - t1}
 
 
 def unet_train_leg(args, dev):
