@@ -11,7 +11,11 @@ moves tensors and keeps the books):
   1. training labels: base flows for seeded (Re, D) pairs by Newton, in
      order of Re, each started from the previous converged flow (parameter
      continuation; the first, and any continuation that fails, from the
-     plain start);
+     plain start).  The Re-sorted pairs are cut into `chains` contiguous
+     runs: the first pair of each run is solved in sequence (each from the
+     previous run's first flow), then the runs continue concurrently, one
+     host thread and CUDA stream each -- a small grid leaves the GPU idle
+     between the launches of one solve, which other solves fill;
   2. train the network on (features, label) pairs with Adam;
   3. for held-out (Re, D): Newton from the network's prediction against
      Newton from the plain start -- selective frequency damping (Sec. 3.1.1,
@@ -26,6 +30,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import threading
 import time
 
 import numpy as np
@@ -91,14 +96,18 @@ def train_step_flops(in_ch: int, width: int, ny: int, nx: int, batch: int) -> in
     return total + 3 * 2 * batch * ny * nx * c[0]
 
 
-def _solve(st, q, args):
+def _sync():
     import torch
 
-    torch.cuda.synchronize()
+    torch.cuda.current_stream().synchronize()   # this thread's stream only (chains run concurrently)
+
+
+def _solve(st, q, args):
+    _sync()
     t0 = time.perf_counter()
     rc, r, it, mv = st.newton_krylov_fixedpoint(q, T=args.T, gmres_m=args.gmres_m, tol=args.tol,
                                                 max_newton=args.max_newton)
-    torch.cuda.synchronize()
+    _sync()
     return {"ok": rc == nsstab.OK, "residual": r, "iters": it, "matvecs": mv, "seconds": time.perf_counter() - t0}
 
 
@@ -107,11 +116,11 @@ def plain_start(st, args):
     import torch
 
     q = torch.zeros(args.ny, args.nx, dtype=torch.float64, device="cuda")
-    torch.cuda.synchronize()
+    _sync()
     t0 = time.perf_counter()
     st.sfd_baseflow(q, chi=args.chi, Delta=args.Delta, tol=0.0, max_steps=args.sfd_steps,
                     check_every=args.sfd_steps)
-    torch.cuda.synchronize()
+    _sync()
     return q, time.perf_counter() - t0
 
 
@@ -135,9 +144,7 @@ def run(args) -> dict:
         rec.update(Re=Re, D=D, sfd_seconds=t_sfd, label=q.clone())
         return rec
 
-    t0 = time.perf_counter()
-    train, prev = [], None
-    for Re, D in sorted(sample_params(args.train, args.seed)):
+    def continue_from(prev, Re, D):
         rec = None
         if prev is not None:
             st = nsstab.Stepper(Re=Re, cyl_D=D, **kw)
@@ -147,9 +154,47 @@ def run(args) -> dict:
             del st
         if rec is None or not rec["ok"]:
             rec = from_plain(Re, D)
+        return rec
+
+    t0 = time.perf_counter()
+    pairs = sorted(sample_params(args.train, args.seed))
+    K = max(1, min(args.chains, len(pairs)))
+    runs = [list(c) for c in np.array_split(np.arange(len(pairs)), K) if len(c)]
+    # the first pair of every run, in sequence
+    heads, prev = [], None
+    for r in runs:
+        rec = continue_from(prev, *pairs[r[0]])
+        heads.append(rec)
         if rec["ok"]:
-            train.append(rec)
             prev = rec["label"]
+    # the rest of every run, runs concurrently (one thread and stream each)
+    results = [[h] for h in heads]
+    errors = []
+
+    def chain(k):
+        import torch
+
+        try:
+            with torch.cuda.stream(torch.cuda.Stream()):
+                prev = heads[k]["label"] if heads[k]["ok"] else None
+                for i in runs[k][1:]:
+                    rec = continue_from(prev, *pairs[i])
+                    results[k].append(rec)
+                    if rec["ok"]:
+                        prev = rec["label"]
+                _sync()
+        except Exception as e:   # reported below; a thread must not die silently
+            errors.append(repr(e))
+
+    threads = [threading.Thread(target=chain, args=(k,)) for k in range(len(runs))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    if errors:
+        raise RuntimeError("label generation failed: " + "; ".join(errors))
+    train = [rec for chain_recs in results for rec in chain_recs if rec["ok"]]
+    t_labels = time.perf_counter() - t0
     test = [from_plain(Re, D) for Re, D in sample_params(args.test, args.seed + 1)]
     t_data = time.perf_counter() - t0
     if not train:
@@ -205,7 +250,7 @@ def run(args) -> dict:
         "unet": {"width": args.width, "params": net.count, "iters": args.iters, "batch": B, "lr": args.lr,
                  "loss_first": losses[0] if losses else None, "loss_last": float(np.mean(losses[-20:])) if losses else None,
                  "train_seconds": t_train, "storage": "bf16 activations, fp32 sums"},
-        "data_seconds": t_data,
+        "data_seconds": t_data, "label_seconds": t_labels, "label_chains": K,
         "newton_iters_mean": {"plain": stat("plain", "iters"), "learned": stat("learned", "iters")},
         "matvecs_mean": {"plain": stat("plain", "matvecs"), "learned": stat("learned", "matvecs")},
         "newton_seconds_mean": {"plain": stat("plain", "seconds"), "learned": stat("learned", "seconds")},
@@ -237,6 +282,7 @@ def parse(argv=None):
     ap.add_argument("--chi", type=float, default=0.1)
     ap.add_argument("--Delta", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--chains", type=int, default=8, help="concurrent continuation runs for the labels")
     return ap.parse_args(argv)
 
 

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 
 def test_pipeline_on_a_small_grid():
     args = learned_guess.parse(["--nx", "32", "--ny", "16", "--train", "8", "--test", "2", "--width", "4",
-                                "--iters", "60", "--batch", "4", "--sfd-steps", "100", "--max-newton", "20"])
+                                "--iters", "60", "--batch", "4", "--sfd-steps", "100", "--max-newton", "20",
+                                "--chains", "3"])
     res = learned_guess.run(args)
     json.dumps(res)
     assert res["train_samples"] >= 6
