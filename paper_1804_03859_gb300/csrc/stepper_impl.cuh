@@ -382,15 +382,19 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
     C* s2 = s + (size_t)CP * S;   // VEL: v^
     const int c0 = blockIdx.x * CP;
-    constexpr int E = 1 << LE;   // CP*ny values over CP*ny/E threads: E each
+    constexpr int E = 1 << LE;   // E elements per thread in each FFT pass
+    // CP*ny values over blockDim threads: E each, or E/2 when the block has
+    // twice the threads of one transform round (both inverse columns at once)
+    const int EL = (CP << logy) / blockDim.x;
     {
         C v[E];
 #pragma unroll
-        for (int it = 0; it < E; ++it) v[it] = f.X1[(size_t)c0 * ny + threadIdx.x + it * blockDim.x];
+        for (int it = 0; it < E; ++it)
+            if (it < EL) v[it] = f.X1[(size_t)c0 * ny + threadIdx.x + it * blockDim.x];
 #pragma unroll
         for (int it = 0; it < E; ++it) {
             const int e = threadIdx.x + it * blockDim.x;
-            s[(e >> logy) * S + sw<T>(e & (ny - 1))] = v[it];
+            if (it < EL) s[(e >> logy) * S + sw<T>(e & (ny - 1))] = v[it];
         }
     }
     __syncthreads();
@@ -454,12 +458,17 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
     C* s2 = s1 + (size_t)CP * S;   // omega^ in, psi*^ out
     C* s3 = s2 + (size_t)CP * S;   // N^{n-1} in
     const int c0i = blockIdx.x * CP;
-    constexpr int E = 1 << LE;   // CP*ny values over CP*ny/E threads: E each
+    constexpr int E = 1 << LE;   // E elements per thread in each FFT pass
+    // CP*ny values over blockDim threads: E each, or E/2 when the block has
+    // twice the threads of one transform round (the inverse transforms of
+    // omega*, psi* (and v*) then run side by side)
+    const int EL = (CP << logy) / blockDim.x;
     // all three input columns are read at once (one wait for the whole block)
     {
         C a[E], b[E], c3[E];
 #pragma unroll
         for (int it = 0; it < E; ++it) {
+            if (it >= EL) continue;
             const size_t g = (size_t)c0i * ny + threadIdx.x + it * blockDim.x;
             a[it] = f.X1[g];
             b[it] = f.Wh[g];
@@ -467,6 +476,7 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
         }
 #pragma unroll
         for (int it = 0; it < E; ++it) {
+            if (it >= EL) continue;
             const int e = threadIdx.x + it * blockDim.x;
             const int o = (e >> logy) * S + sw<T>(e & (ny - 1));
             s1[o] = a[it];
@@ -627,6 +637,7 @@ __global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, s
 // block, 2^le elements per thread in the FFT passes; grid.y = members.
 struct Launch {
     int blocks = 0, threads = 0, per = 0, logper = 0, le = 3;
+    int tm = 1;            // column passes: threads per block = tm x one transform round
     size_t smem = 0;
     bool ok = false;
 };
@@ -748,7 +759,9 @@ class StepperImpl : public StepperBase {
         red_host_ = nullptr;
     }
     int build_tables();
-    Launch make_plan(int kid, int le, int per) const;
+    Launch make_plan(int kid, int le, int per, int tm = 1) const;
+    Launch with_tm2(int kid, const Launch& L) const;
+    int set_plan_tm(int kid, int le, int per, int tm);
     Launch default_plan(int kid) const;
     int set_smem_attr(int kid, const Launch& L);
 
@@ -785,8 +798,15 @@ template <class T> static int seq_count(int kid, int nx, int ny) {
     }
 }
 
-template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) const {
+// Column passes with two or more inverse transforms per column (col_update;
+// col_poisson of the FP32 stepper) may run blocks of twice the threads of
+// one transform round (tm = 2): the inverse transforms then proceed side by
+// side, and twice the loads are in flight.
+template <class T> static bool tm2_allowed(int kid) { return kid == KCOLU || (kid == KCOLP && kF32<T>); }
+
+template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per, int tm) const {
     Launch L;
+    if (tm != 1 && !(tm == 2 && tm2_allowed<T>(kid))) return L;
     const bool row = (kid == KINVP || kid == KFWDR || kid == KINVR || kid == KFWDP);
     const int N = row ? nx_ : ny_;
     const int logN = row ? ilog2(nx_) : ilog2(ny_);
@@ -795,13 +815,14 @@ template <class T> Launch StepperImpl<T>::make_plan(int kid, int le, int per) co
     const int nseq_smem = (kid == KCOLU) ? 3 : (kid == KCOLP && kF32<T>) ? 2 : 1;
     if (le < 1 || le > 3 || logN < le || per < 1 || !is_pow2(per) || per > count) return L;
     if (kF32<T> && kid == KINVR && per > ny_ / 2) return L;   // blocks must not straddle the two parts
-    const int threads = per * (N >> le);
+    const int threads = per * (N >> le) * tm;
     const int rp = row ? per : ((N >> le) < 32 ? 32 / (N >> le) : 1);
     const size_t smem = (size_t)per * nseq_smem * seq_stride(N, rp, (int)sizeof(C) / 4) * sizeof(C);
     if (threads > 1024 || smem > kMaxSmem) return L;
     L.per = per;
     L.logper = ilog2(per);
     L.le = le;
+    L.tm = tm;
     L.blocks = count / per;
     L.threads = threads;
     L.smem = smem;
@@ -825,7 +846,14 @@ template <class T> Launch StepperImpl<T>::default_plan(int kid) const {
     Launch L = make_plan(kid, le, per);
     while ((!L.ok || L.threads > max_threads_for<T>(kid, le)) && per > 1) L = make_plan(kid, le, per /= 2);
     while ((!L.ok || L.threads > max_threads_for<T>(kid, le)) && le > 1) L = make_plan(kid, --le, 1);
-    return L;
+    return with_tm2(kid, L);
+}
+
+// The same plan with tm = 2 where the kernel allows it and the block fits.
+template <class T> Launch StepperImpl<T>::with_tm2(int kid, const Launch& L) const {
+    if (!L.ok || !tm2_allowed<T>(kid)) return L;
+    const Launch L2 = make_plan(kid, L.le, L.per, 2);
+    return (L2.ok && L2.threads <= max_threads_for<T>(kid, L.le)) ? L2 : L;
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel function,
@@ -888,7 +916,11 @@ template <class T> int StepperImpl<T>::set_plan(int kid, int le, int per) {
         set_error("set_plan: bad kernel id");
         return NSSTAB_ERR_INVALID_ARG;
     }
-    const Launch L = make_plan(kid, le, per);
+    return set_plan_tm(kid, le, per, with_tm2(kid, make_plan(kid, le, per)).tm);
+}
+
+template <class T> int StepperImpl<T>::set_plan_tm(int kid, int le, int per, int tm) {
+    const Launch L = make_plan(kid, le, per, tm);
     if (!L.ok || L.threads > max_threads_for<T>(kid, le)) {
         set_error("set_plan: configuration not valid for this grid");
         return NSSTAB_ERR_INVALID_ARG;
@@ -1172,7 +1204,7 @@ template <class T> int StepperImpl<T>::init() {
             set_error("grid too large for the shared-memory FFT");
             return NSSTAB_ERR_INVALID_ARG;
         }
-        NS_TRY(set_plan(k, L.le, L.per));
+        NS_TRY(set_plan_tm(k, L.le, L.per, L.tm));
     }
     NS_CUDA(cudaStreamSynchronize(stream_));
     return NSSTAB_OK;
@@ -1369,18 +1401,20 @@ template <class T> int StepperImpl<T>::autotune(int reps, int* chosen) {
         float best_ms = 1e30f;
         for (int le = 1; le <= 3; ++le) {
             for (int per = 1; per <= 16; per *= 2) {
-                const Launch L = make_plan(kid, le, per);
-                if (!L.ok || L.threads < 32 || L.threads > max_threads_for<T>(kid, le)) continue;
-                NS_TRY(set_smem_attr(kid, L));
-                float ms = 0.f;
-                NS_TRY(time_kernel(kid, L, reps, &ms));
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best = L;
+                for (int tm = 1; tm <= 2; ++tm) {
+                    const Launch L = make_plan(kid, le, per, tm);
+                    if (!L.ok || L.threads < 32 || L.threads > max_threads_for<T>(kid, le)) continue;
+                    NS_TRY(set_smem_attr(kid, L));
+                    float ms = 0.f;
+                    NS_TRY(time_kernel(kid, L, reps, &ms));
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best = L;
+                    }
                 }
             }
         }
-        NS_TRY(set_plan(kid, best.le, best.per));
+        NS_TRY(set_plan_tm(kid, best.le, best.per, best.tm));
         if (chosen) {
             chosen[2 * kid] = best.le;
             chosen[2 * kid + 1] = best.per;
