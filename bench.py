@@ -472,6 +472,7 @@ def run_native(args, rank: int, world: int):
         serving = serve_leg(args, dev)
     unet_leg = None if args.no_serve else unet_train_leg(args, dev)
     newton_leg = None if (args.no_serve or args.no_eigs) else newton_leg_run(args, dev)
+    wake_leg = None if (args.no_serve or args.no_eigs) else wake_stability_leg(args, dev)
 
     if rank != 0:
         return
@@ -510,6 +511,7 @@ def run_native(args, rank: int, world: int):
         "serving": serving,
         "unet": unet_leg,
         "newton": newton_leg,
+        "wake_stability": wake_leg,
     }
     print(json.dumps(out))
 
@@ -539,6 +541,40 @@ def newton_leg_run(args, dev):
             "jacobian": "exact tangent (co-integrated), f32", "start": "300 SFD steps from rest (chi 0.1, Delta 0.5)",
             "status": rc, "residual": r, "newton_iters": it, "jacobian_products": mv, "sfd_seconds": t1 - t0,
             "newton_seconds": t2 - t1}
+
+
+def wake_stability_leg(args, dev):
+    """The 128x64 cylinder case end to end: for Re 40, 50, 60 the steady base
+    flow by Newton-Krylov (exact tangent, from 300 SFD steps), then the
+    leading eigenvalues mu of M = exp(T A) about it (Krylov-Schur, m 64,
+    nev 4, tol 1e-10, T 0.5), reported as growth rate Re(log mu)/T and
+    frequency Im(log mu)/T of the leading mode."""
+    import torch
+
+    from paper_1804_03859_gb300 import inputs, nsstab
+
+    out = []
+    for re in (40.0, 50.0, 60.0):
+        kw = dict(nx=128, ny=64, dt=0.01, Re=re)
+        st = nsstab.Stepper(**kw)
+        q = torch.zeros(64, 128, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st.sfd_baseflow(q, chi=0.1, Delta=0.5, tol=0.0, max_steps=300, check_every=300)
+        rc, r, it, mv = st.newton_krylov_fixedpoint(q, T=0.4, gmres_m=50, tol=1e-10, max_newton=30)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        v0 = torch.from_numpy(inputs.gaussian_field(64, 128, seed=0)).to(dev)
+        e = st.arnoldi_eigs(q, v0, m=64, nev=4, tol=1e-10, T=0.5, max_restarts=40)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        lam = e.growth(0.5)
+        out.append({"Re": re, "base_flow": {"status": rc, "residual": r, "newton_iters": it, "seconds": t1 - t0},
+                    "eigs": {"n_conv": e.n_conv, "n_matvec": e.n_matvec, "seconds": t2 - t1,
+                             "mu": [[float(m.real), float(m.imag)] for m in e.mu],
+                             "leading_growth_rate": float(lam[0].real), "leading_frequency": float(abs(lam[0].imag))}})
+    return {"workload": "cylinder wake 128x64, dt 0.01, Re 40/50/60: Newton base flow + leading eigenvalues",
+            "cases": out}
 
 
 def unet_train_leg(args, dev):
