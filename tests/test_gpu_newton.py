@@ -97,3 +97,26 @@ def test_newton_rejects_mismatched_steppers():
     q = torch.zeros(16, 32, dtype=torch.float64, device="cuda")
     with pytest.raises(nsstab.NsstabError):
         st.newton_krylov_fixedpoint(q, T=0.4, gmres_m=10, tol=1e-10, max_newton=2, lin=other)
+
+
+def test_cylinder_wake_leading_mode_is_the_shedding_pair():
+    """Newton base flows at Re 40 and 60 (128x64) and the leading eigenvalues
+    of M about them: a complex pair at the shedding frequency (St = omega/2pi
+    in [0.11, 0.16] for D = U = 1), whose growth rate rises with Re."""
+    growth = []
+    for re in (40.0, 60.0):
+        st = nsstab.Stepper(nx=128, ny=64, dt=0.01, Re=re)
+        q = torch.zeros(64, 128, dtype=torch.float64, device="cuda")
+        st.sfd_baseflow(q, chi=0.1, Delta=0.5, tol=0.0, max_steps=300, check_every=300)
+        rc, r, iters, mv = st.newton_krylov_fixedpoint(q, T=0.4, gmres_m=50, tol=1e-10, max_newton=30)
+        assert rc == nsstab.OK and r <= 1e-10
+        got = q.cpu().numpy()
+        mirror = got[(-np.arange(64)) % 64, :]
+        assert np.abs(got + mirror).max() <= 1e-8 * np.abs(got).max()   # symmetric steady wake
+        e = st.arnoldi_eigs(q, _dev(inputs.gaussian_field(64, 128, seed=0)), m=64, nev=2, tol=1e-10, T=0.5,
+                            max_restarts=40)
+        assert e.n_conv == len(e.mu)
+        lam = e.growth(0.5)[0]
+        assert e.mu[0].imag != 0.0 and 0.11 <= abs(lam.imag) / (2 * np.pi) <= 0.16
+        growth.append(lam.real)
+    assert growth[1] > growth[0]
