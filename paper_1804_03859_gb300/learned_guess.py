@@ -51,7 +51,7 @@ def features(nx: int, ny: int, Re: float, D: float, Lx: float = 16.0, Ly: float 
     ddy = (y - cyl_y + 0.5 * Ly) % Ly - 0.5 * Ly
     r2 = ddx[None, :] ** 2 + ddy[:, None] ** 2
     bump = np.exp(-r2 / (0.5 * D) ** 2)
-    return np.stack([bump, np.full((ny, nx), (Re - 80.0) / 40.0), np.full((ny, nx), (D - 1.0) / 0.2)])
+    return np.stack([bump, np.full((ny, nx), (Re - 95.0) / 55.0), np.full((ny, nx), (D - 1.0) / 0.2)])
 
 
 def he_init(in_ch: int, width: int, seed: int) -> np.ndarray:
@@ -124,9 +124,9 @@ def plain_start(st, args):
     return q, time.perf_counter() - t0
 
 
-def sample_params(n: int, seed: int):
+def sample_params(n: int, seed: int, re_min: float = 40.0, re_max: float = 150.0):
     rng = np.random.default_rng(seed)
-    return [(float(rng.uniform(40.0, 120.0)), float(rng.uniform(0.8, 1.2))) for _ in range(n)]
+    return [(float(rng.uniform(re_min, re_max)), float(rng.uniform(0.8, 1.2))) for _ in range(n)]
 
 
 def run(args) -> dict:
@@ -157,7 +157,7 @@ def run(args) -> dict:
         return rec
 
     t0 = time.perf_counter()
-    pairs = sorted(sample_params(args.train, args.seed))
+    pairs = sorted(sample_params(args.train, args.seed, args.re_min, args.re_max))
     K = max(1, min(args.chains, len(pairs)))
     runs = [list(c) for c in np.array_split(np.arange(len(pairs)), K) if len(c)]
     # the first pair of every run, in sequence
@@ -195,7 +195,7 @@ def run(args) -> dict:
         raise RuntimeError("label generation failed: " + "; ".join(errors))
     train = [rec for chain_recs in results for rec in chain_recs if rec["ok"]]
     t_labels = time.perf_counter() - t0
-    test = [from_plain(Re, D) for Re, D in sample_params(args.test, args.seed + 1)]
+    test = [from_plain(Re, D) for Re, D in sample_params(args.test, args.seed + 1, args.re_min, args.re_max)]
     t_data = time.perf_counter() - t0
     if not train:
         return {"error": "no training base flow converged"}
@@ -243,7 +243,7 @@ def run(args) -> dict:
         return float(np.mean(v)) if v else None
 
     return {
-        "workload": f"learned Newton start, {args.nx}x{args.ny}, Re U[40,120], D U[0.8,1.2]",
+        "workload": f"learned Newton start, {args.nx}x{args.ny}, Re U[{args.re_min:g},{args.re_max:g}], D U[0.8,1.2]",
         "grid": [args.nx, args.ny], "dt": dt, "T": args.T, "gmres_m": args.gmres_m, "tol": args.tol,
         "sfd_start": {"steps": args.sfd_steps, "chi": args.chi, "Delta": args.Delta},
         "train_samples": len(train), "train_requested": args.train, "test_samples": len(test),
@@ -283,6 +283,8 @@ def parse(argv=None):
     ap.add_argument("--Delta", type=float, default=0.5)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--chains", type=int, default=8, help="concurrent continuation runs for the labels")
+    ap.add_argument("--re-min", dest="re_min", type=float, default=40.0)
+    ap.add_argument("--re-max", dest="re_max", type=float, default=150.0)
     return ap.parse_args(argv)
 
 
