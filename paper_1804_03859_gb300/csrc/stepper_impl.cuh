@@ -62,16 +62,6 @@ enum RowMode { FWD_PLAIN = 0, FWD_RHS_NL = 1, FWD_RHS_LIN = 2, FWD_PEN_NL = 3, F
 // transforms also split twiddles into hi + lo; see fft.cuh.)
 template <class T> constexpr bool kF32 = std::is_same<T, float>::value;
 
-// Programmatic dependent launch (the step kernels are launched with
-// programmatic stream serialization).  pdl_wait, before a kernel's first
-// global-memory access, waits until the previous kernel on the stream has
-// completed and its writes are visible (a kernel launched without the
-// attribute passes straight through); pdl_trigger, just before a kernel's
-// final stores, lets the next kernel be scheduled, so that its launch
-// overlaps only this kernel's store phase and teardown.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 template <class T> struct Fields {
     int nx, ny, nxh, logx, logy;
     int bper;              // members per parameter set (member m uses set m / bper)
@@ -233,7 +223,6 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
 
 template <class T, int MODE, int LE>
 __global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
-    pdl_wait();
     using C = Cx<T>;
     if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -270,7 +259,6 @@ __global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool
     if (!do_fft) return;
     __syncthreads();
     fft_smem<false, T, LE>(s, f.logx, S, RP, f.twx[LE]);
-    pdl_trigger();
     // split Z = FFT(a + i b) into the half-spectra of a and b
     const int nh = nx >> 1;
 #pragma unroll
@@ -307,7 +295,6 @@ enum InvIO {
 // Inverse x-transform of RP sequences per block, as selected by IO.
 template <class T, int LE, int IO>
 __global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP) {
-    pdl_wait();
     using C = Cx<T>;
     if (!member_view(f)) return;
     int pair0 = blockIdx.x * RP;
@@ -355,7 +342,6 @@ __global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP) {
     }
     __syncthreads();
     fft_smem<true, T, LE>(s, f.logx, S, RP, f.twx[LE]);
-    pdl_trigger();
 #pragma unroll
     for (int it = 0; it < E; ++it) {
         const int e = threadIdx.x + it * blockDim.x;
@@ -388,7 +374,6 @@ __device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
 // column).
 template <class T, int LE, bool VEL>
 __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
-    pdl_wait();
     using C = Cx<T>;
     if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -449,7 +434,6 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     }
     __syncthreads();
     fft_smem<true, T, LE>(s, logy, S, VEL ? 2 * CP : CP, f.twy[LE]);
-    pdl_trigger();
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
         const size_t g = (size_t)(c0 + c) * ny + j;
@@ -465,7 +449,6 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
 // v*^ -> X3, as in k_col_poisson).
 template <class T, int LE>
 __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
-    pdl_wait();
     using C = Cx<T>;
     if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -570,7 +553,6 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
     }
     __syncthreads();
     fft_smem<true, T, LE>(s1, logy, S, (kF32<T> ? 3 : 2) * CP, f.twy[LE]);
-    pdl_trigger();
     for (int e = threadIdx.x; e < (CP << logy); e += blockDim.x) {
         const int c = e >> logy, j = e & (ny - 1);
         const size_t g = (size_t)(c0i + c) * ny + j;
@@ -586,8 +568,6 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
 // (kVel: the base velocity) held in member slot blockIdx.y of W and P (U, V).
 template <class T>
 __global__ void k_base_fields(Fields<T> f, T* Ub, T* Vb, T* DxOb, T* DyOb) {
-    pdl_wait();
-    pdl_trigger();
     const size_t n = (size_t)f.nx * f.ny;
     const size_t off = (size_t)blockIdx.y * f.fs;
     const T* P = f.P + off;   // Psi_b
@@ -683,23 +663,6 @@ static const size_t kMaxSmem = 200 * 1024;
 #define K_COLP(le) k_col_poisson<T, le, kF32<T>>
 #define K_COLPSI(le) k_col_poisson<T, le, false>
 #define K_COLU(le) k_col_update<T, le>
-
-// Launch with programmatic stream serialization (see pdl_wait / pdl_trigger).
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kernel)(KArgs...), dim3 grid, unsigned threads, size_t smem, cudaStream_t st,
-                       Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);   // errors are read by NS_LAUNCH_CHECK
-}
 
 template <class T>
 class StepperImpl : public StepperBase {
@@ -978,7 +941,7 @@ template <class T> int StepperImpl<T>::set_plan_tm(int kid, int le, int per, int
 template <class T> int StepperImpl<T>::launch_plain(cudaStream_t st) {
     const Launch& L = plan_[KFWDR];
     const dim3 g(L.blocks, B_);
-#define CALL_PLAIN(le) launch_pdl(k_row_forward<T, FWD_PLAIN, le>, g, L.threads, L.smem, st, f_, L.per, L.logper, false, true)
+#define CALL_PLAIN(le) k_row_forward<T, FWD_PLAIN, le><<<g, L.threads, L.smem, st>>>(f_, L.per, L.logper, false, true)
     NS_DISPATCH_LE(L, CALL_PLAIN);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
@@ -991,18 +954,18 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
     if (act_override_) fl.active = act_override_;
     switch (kid) {
         case KCOLP: {
-#define CALL_COLP(le) launch_pdl(k_col_poisson<T, le, kF32<T>>, g, L.threads, L.smem, st, fl, L.per, scale_)
+#define CALL_COLP(le) k_col_poisson<T, le, kF32<T>><<<g, L.threads, L.smem, st>>>(fl, L.per, scale_)
             NS_DISPATCH_LE(L, CALL_COLP);
             break;
         }
         case KINVP: {
-#define CALL_INVP(le) launch_pdl(K_INVP(le), g, L.threads, L.smem, st, fl, L.per, L.logper)
+#define CALL_INVP(le) K_INVP(le)<<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper)
             NS_DISPATCH_LE(L, CALL_INVP);
             break;
         }
         case KFWDR: {
-#define CALL_FRL(le) launch_pdl(k_row_forward<T, FWD_RHS_LIN, le>, g, L.threads, L.smem, st, fl, L.per, L.logper, false, true)
-#define CALL_FRN(le) launch_pdl(k_row_forward<T, FWD_RHS_NL, le>, g, L.threads, L.smem, st, fl, L.per, L.logper, false, true)
+#define CALL_FRL(le) k_row_forward<T, FWD_RHS_LIN, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, false, true)
+#define CALL_FRN(le) k_row_forward<T, FWD_RHS_NL, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, false, true)
             if (linear) {
                 NS_DISPATCH_LE(L, CALL_FRL);
             } else {
@@ -1012,18 +975,18 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
         }
         case KCOLU: {
             const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
-#define CALL_COLU(le) launch_pdl(k_col_update<T, le>, g, L.threads, L.smem, st, fl, L.per, c1, c0, first)
+#define CALL_COLU(le) k_col_update<T, le><<<g, L.threads, L.smem, st>>>(fl, L.per, c1, c0, first)
             NS_DISPATCH_LE(L, CALL_COLU);
             break;
         }
         case KINVR: {
-#define CALL_INVR(le) launch_pdl(K_INVR(le), g, L.threads, L.smem, st, fl, L.per, L.logper)
+#define CALL_INVR(le) K_INVR(le)<<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper)
             NS_DISPATCH_LE(L, CALL_INVR);
             break;
         }
         default: {
-#define CALL_FPL(le) launch_pdl(k_row_forward<T, FWD_PEN_LIN, le>, g, L.threads, L.smem, st, fl, L.per, L.logper, sfd, do_fft)
-#define CALL_FPN(le) launch_pdl(k_row_forward<T, FWD_PEN_NL, le>, g, L.threads, L.smem, st, fl, L.per, L.logper, sfd, do_fft)
+#define CALL_FPL(le) k_row_forward<T, FWD_PEN_LIN, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, sfd, do_fft)
+#define CALL_FPN(le) k_row_forward<T, FWD_PEN_NL, le><<<g, L.threads, L.smem, st>>>(fl, L.per, L.logper, sfd, do_fft)
             if (linear) {
                 NS_DISPATCH_LE(L, CALL_FPL);
             } else {
@@ -1301,7 +1264,7 @@ template <class T> int StepperImpl<T>::psi_function(cudaStream_t st) {
     if (!kF32<T>) return stream_function(st);
     const Launch& Lc = plan_[KCOLP];
     const dim3 gc(Lc.blocks, B_);
-#define CALL_COLPSI(le) launch_pdl(k_col_poisson<T, le, false>, gc, Lc.threads, Lc.smem, st, f_, Lc.per, scale_)
+#define CALL_COLPSI(le) k_col_poisson<T, le, false><<<gc, Lc.threads, Lc.smem, st>>>(f_, Lc.per, scale_)
     NS_DISPATCH_LE(Lc, CALL_COLPSI);
     NS_LAUNCH_CHECK();
     Launch L = plan_[KINVP];   // ny rows -> ny/2 row pairs, each block at most as large
@@ -1311,7 +1274,7 @@ template <class T> int StepperImpl<T>::psi_function(cudaStream_t st) {
     L.threads = L.per * (nx_ >> L.le);
     L.smem = (size_t)L.per * seq_stride(nx_, L.per, (int)sizeof(C) / 4) * sizeof(C);
     const dim3 gr(L.blocks, B_);
-#define CALL_INVPSI(le) launch_pdl(K_INVPSI(le), gr, L.threads, L.smem, st, f_, L.per, L.logper)
+#define CALL_INVPSI(le) K_INVPSI(le)<<<gr, L.threads, L.smem, st>>>(f_, L.per, L.logper)
     NS_DISPATCH_LE(L, CALL_INVPSI);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
@@ -1331,8 +1294,8 @@ int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool s
             const bool first = first_ab1 && s == 0;
             const bool fft = fft_last || (s + 1 < nsteps);
             NS_TRY(stream_function(st));
-            launch_pdl(k_base_fields<T>, dim3(kPtBlocks, 1), 256, 0, st, f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb,
-                       (T*)f_.DyOb);
+            k_base_fields<T><<<dim3(kPtBlocks, 1), 256, 0, st>>>(f_, (T*)f_.Ub, (T*)f_.Vb, (T*)f_.DxOb,
+                                                                 (T*)f_.DyOb);
             NS_LAUNCH_CHECK();
             act_override_ = tmask_;
             int rc = launch(KFWDR, st, false, false, true, first);
