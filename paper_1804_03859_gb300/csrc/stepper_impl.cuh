@@ -849,9 +849,13 @@ template <class T> Launch StepperImpl<T>::default_plan(int kid) const {
     return with_tm2(kid, L);
 }
 
-// The same plan with tm = 2 where the kernel allows it and the block fits.
+// The same plan with tm = 2 where the kernel allows it, the block fits, and
+// the grid is short of warps (fewer than 8 per SM at tm = 1 over the whole
+// batch): doubling the block pays for latency-bound small grids, while on
+// large grids it only raises the register pressure.
 template <class T> Launch StepperImpl<T>::with_tm2(int kid, const Launch& L) const {
     if (!L.ok || !tm2_allowed<T>(kid)) return L;
+    if ((long)B_ * L.blocks * L.threads >= 8L * 152 * 32) return L;
     const Launch L2 = make_plan(kid, L.le, L.per, 2);
     return (L2.ok && L2.threads <= max_threads_for<T>(kid, L.le)) ? L2 : L;
 }
