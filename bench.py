@@ -607,7 +607,8 @@ def unet_train_leg(args, dev):
     return {"grid": [nx, ny], "batch": B, "width": width, "params": net.count, "ms_per_train_step": ms,
             "flops_per_step": fl, "tflops": fl / (ms * 1e-3) / 1e12, "fp32_fma_peak_tflops": fp32,
             "frac_of_fp32_peak": fl / (ms * 1e-3) / 1e12 / fp32,
-            "kernels": "direct FP32-FMA convolutions on bf16 activations (not tensor cores)"}
+            "kernels": ("3x3 convolutions (forward, input and weight gradients) as implicit GEMMs on the tensor cores: "
+                        "BF16 mma.sync, FP32 accumulation, FP32 gradients split bf16 hi + lo")}
 
 
 SERVE_JOBS = 24

@@ -7,15 +7,16 @@
 // every sum in FP32; gradients of activations in FP32.
 //
 // Kernels (one pass each, no im2col buffer):
-//   k_conv_fwd       3x3 periodic convolution + bias + ReLU: a thread owns
-//                    one point and 8 output channels; the weights of the
-//                    8 channels for a chunk of 32 input channels are staged
-//                    in shared memory (FP32) and read as broadcasts
-//   k_conv_bwd_data  gradient of the input: the same shape with the roles of
-//                    the channels exchanged and the taps mirrored
-//   k_conv_bwd_w     gradient of the weights and bias: a block owns a 16 x 16
-//                    (output, input channel) tile and a chunk of points,
-//                    9 tap sums per thread, added to the FP32 gradient
+//   k_conv_fwd       3x3 periodic convolution + bias + ReLU on the tensor
+//                    cores: implicit GEMM in BF16 mma.sync steps with FP32
+//                    accumulation (64 points x 32 output channels a block)
+//   k_conv_bwd_data  gradient of the input on the tensor cores: the same
+//                    implicit GEMM with the channels exchanged and the taps
+//                    mirrored, the FP32 gradient split into bf16 hi + lo
+//   k_conv_bwd_w     gradient of the weights and bias on the tensor cores:
+//                    a block owns 32 x 32 (output, input) channels, all 9
+//                    taps and a chunk of points (split reduction, atomicAdd
+//                    into the FP32 gradient)
 //   pooling, upsampling with concatenation, their adjoints, the 1x1 output
 //   layer, the mean-squared loss and Adam are pointwise kernels.
 // The layer sequence and every rounding point follow the oracle's
@@ -33,9 +34,6 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 constexpr int kLevels = 4;
-constexpr int kCoTile = 8;      // output channels per thread in k_conv_fwd
-constexpr int kCiChunk = 32;    // input channels per shared-memory stage
-constexpr int kFwdThreads = 128;
 
 struct ConvDesc {
     int ci = 0, co = 0, k = 3;   // k = 3 (3x3) or 1 (the output layer)
@@ -53,112 +51,261 @@ __device__ __forceinline__ long nbr(long p, int lh, int lw, int dy, int dx) {
 }
 
 // out[p][co] = relu(bias[co] + sum_{tap, ci} w[co][ci][tap] in[nbr(p, tap)][ci])
-__global__ void k_conv_fwd(const bf16* __restrict__ in, const bf16* __restrict__ w, const float* __restrict__ bias,
-                           bf16* __restrict__ out, long P, int lh, int lw, int Ci, int Co) {
-    __shared__ float ws[9][kCiChunk][kCoTile];
-    const long p = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const int co0 = blockIdx.y * kCoTile;
-    float acc[kCoTile];
+// on the tensor cores: an implicit GEMM (rows = points, columns = output
+// channels, reduction = 9 taps x input channels) in BF16 mma.sync m16n8k16
+// steps with FP32 accumulation.  A block of 4 warps owns 64 points x 32
+// output channels; each warp 16 points x 4 n-tiles of 8.  The A fragments
+// (the 16 input channels of a point's neighbour at one tap) are read from
+// global memory (L1/L2 resident); the weights of the block's 32 output
+// channels for a chunk of 16 input channels and all 9 taps are staged in
+// shared memory, rows padded so that the B-fragment loads of a warp hit 32
+// distinct banks.  Products of bfloat16 values are exact in FP32, so only
+// the order of the FP32 sums differs from a scalar loop.
+constexpr int kMmaPix = 64, kMmaCo = 32, kMmaK = 16, kMmaPad = 8;
+
+__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// channels k, k+1 of the point at offset nb (nb < 0: no point), zero beyond Ci
+__device__ __forceinline__ uint32_t ld_a(const bf16* __restrict__ in, long nb, int k, int Ci) {
+    if (nb < 0) return 0u;
+    const bf16 z = __float2bfloat16_rn(0.f);
+    const bf16 lo = (k < Ci) ? in[nb + k] : z;
+    const bf16 hi = (k + 1 < Ci) ? in[nb + k + 1] : z;
+    return pack_bf16(lo, hi);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ in, const bf16* __restrict__ w,
+                                                  const float* __restrict__ bias, bf16* __restrict__ out, long P,
+                                                  int lh, int lw, int Ci, int Co) {
+    __shared__ __align__(16) bf16 ws[9][kMmaCo][kMmaK + kMmaPad];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const long p0 = (long)blockIdx.x * kMmaPix + warp * 16 + gid;   // rows gid and gid + 8 of the warp's tile
+    const long p1 = p0 + 8;
+    const int co0 = blockIdx.y * kMmaCo;
+    long nb0[9], nb1[9];
 #pragma unroll
-    for (int c = 0; c < kCoTile; ++c) acc[c] = (co0 + c < Co) ? bias[co0 + c] : 0.f;
-    long nb[9];
-    if (p < P) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) nb[t] = nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci;
+    for (int t = 0; t < 9; ++t) {
+        nb0[t] = (p0 < P) ? nbr(p0, lh, lw, t / 3 - 1, t % 3 - 1) * Ci : -1;
+        nb1[t] = (p1 < P) ? nbr(p1, lh, lw, t / 3 - 1, t % 3 - 1) * Ci : -1;
     }
-    for (int c0 = 0; c0 < Ci; c0 += kCiChunk) {
-        const int nci = min(kCiChunk, Ci - c0);
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+    for (int c0 = 0; c0 < Ci; c0 += kMmaK) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 9 * kCiChunk * kCoTile; e += blockDim.x) {
-            const int c = e % kCoTile, ci = (e / kCoTile) % kCiChunk, t = e / (kCoTile * kCiChunk);
-            const int co = co0 + c;
-            ws[t][ci][c] = (ci < nci && co < Co) ? __bfloat162float(w[((long)co * Ci + c0 + ci) * 9 + t]) : 0.f;
+        for (int e = threadIdx.x; e < 9 * kMmaCo * kMmaK; e += blockDim.x) {
+            const int k = e % kMmaK, co = (e / kMmaK) % kMmaCo, t = e / (kMmaK * kMmaCo);
+            const int gco = co0 + co, gci = c0 + k;
+            ws[t][co][k] = (gco < Co && gci < Ci) ? w[((long)gco * Ci + gci) * 9 + t] : __float2bfloat16_rn(0.f);
         }
         __syncthreads();
-        if (p < P) {
 #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const bf16* src = in + nb[t] + c0;
-                for (int ci = 0; ci < nci; ++ci) {
-                    const float a = __bfloat162float(src[ci]);
+        for (int t = 0; t < 9; ++t) {
+            const int k0 = c0 + 2 * tig, k1 = k0 + 8;
+            const uint32_t a0 = ld_a(in, nb0[t], k0, Ci), a1 = ld_a(in, nb1[t], k0, Ci);
+            const uint32_t a2 = ld_a(in, nb0[t], k1, Ci), a3 = ld_a(in, nb1[t], k1, Ci);
 #pragma unroll
-                    for (int c = 0; c < kCoTile; ++c) acc[c] = fmaf(a, ws[t][ci][c], acc[c]);
-                }
+            for (int j = 0; j < 4; ++j) {
+                const bf16* row = &ws[t][j * 8 + gid][0];
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row + 2 * tig);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 2 * tig + 8);
+                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
             }
         }
     }
-    if (p < P) {
 #pragma unroll
-        for (int c = 0; c < kCoTile; ++c)
-            if (co0 + c < Co) out[p * Co + co0 + c] = __float2bfloat16_rn(fmaxf(acc[c], 0.f));
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int co = co0 + j * 8 + 2 * tig + h;
+            if (co >= Co) continue;
+            const float b = bias[co];
+            if (p0 < P) out[p0 * Co + co] = __float2bfloat16_rn(fmaxf(acc[j][h] + b, 0.f));
+            if (p1 < P) out[p1 * Co + co] = __float2bfloat16_rn(fmaxf(acc[j][2 + h] + b, 0.f));
+        }
     }
 }
 
-// gin[q][ci] = sum_{tap, co} w[co][ci][tap] gz[q - tap offset][co]
-__global__ void k_conv_bwd_data(const float* __restrict__ gz, const bf16* __restrict__ w, float* __restrict__ gin,
-                                long P, int lh, int lw, int Ci, int Co) {
-    __shared__ float ws[9][kCiChunk][kCoTile];   // [tap][co in chunk][ci in tile]
-    const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    const int ci0 = blockIdx.y * kCoTile;
-    float acc[kCoTile];
-#pragma unroll
-    for (int c = 0; c < kCoTile; ++c) acc[c] = 0.f;
-    long nb[9];
-    if (q < P) {
-#pragma unroll
-        for (int t = 0; t < 9; ++t) nb[t] = nbr(q, lh, lw, 1 - t / 3, 1 - t % 3) * Co;
+// gin[q][ci] = sum_{tap, co} w[co][ci][tap] gz[q - tap offset][co], on the
+// tensor cores like k_conv_fwd (rows = points, columns = input channels,
+// reduction = taps x output channels).  The FP32 gradient enters the BF16
+// products split as hi + lo (hi = its bfloat16 rounding, lo = the bfloat16
+// rounding of the rest), two mma steps per fragment: about 16 significant
+// bits of every product, summed in FP32.
+__device__ __forceinline__ void split_pair(const float* __restrict__ g, long nb, int k, int Co, uint32_t& hi,
+                                           uint32_t& lo) {
+    float x = 0.f, y = 0.f;
+    if (nb >= 0) {
+        if (k < Co) x = g[nb + k];
+        if (k + 1 < Co) y = g[nb + k + 1];
     }
-    for (int c0 = 0; c0 < Co; c0 += kCiChunk) {
-        const int nco = min(kCiChunk, Co - c0);
+    const bf16 xh = __float2bfloat16_rn(x), yh = __float2bfloat16_rn(y);
+    hi = pack_bf16(xh, yh);
+    lo = pack_bf16(__float2bfloat16_rn(x - __bfloat162float(xh)), __float2bfloat16_rn(y - __bfloat162float(yh)));
+}
+
+__global__ void __launch_bounds__(128) k_conv_bwd_data(const float* __restrict__ gz, const bf16* __restrict__ w,
+                                                       float* __restrict__ gin, long P, int lh, int lw, int Ci,
+                                                       int Co) {
+    __shared__ __align__(16) bf16 ws[9][kMmaCo][kMmaK + kMmaPad];   // [tap][input channel][output channel]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const long q0 = (long)blockIdx.x * kMmaPix + warp * 16 + gid;
+    const long q1 = q0 + 8;
+    const int ci0 = blockIdx.y * kMmaCo;
+    long nb0[9], nb1[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+        nb0[t] = (q0 < P) ? nbr(q0, lh, lw, 1 - t / 3, 1 - t % 3) * Co : -1;
+        nb1[t] = (q1 < P) ? nbr(q1, lh, lw, 1 - t / 3, 1 - t % 3) * Co : -1;
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+    for (int c0 = 0; c0 < Co; c0 += kMmaK) {
         __syncthreads();
-        for (int e = threadIdx.x; e < 9 * kCiChunk * kCoTile; e += blockDim.x) {
-            const int c = e % kCoTile, co = (e / kCoTile) % kCiChunk, t = e / (kCoTile * kCiChunk);
-            const int ci = ci0 + c;
-            ws[t][co][c] = (co < nco && ci < Ci) ? __bfloat162float(w[((long)(c0 + co) * Ci + ci) * 9 + t]) : 0.f;
+        for (int e = threadIdx.x; e < 9 * kMmaCo * kMmaK; e += blockDim.x) {
+            const int k = e % kMmaK, ci = (e / kMmaK) % kMmaCo, t = e / (kMmaK * kMmaCo);
+            const int gci = ci0 + ci, gco = c0 + k;
+            ws[t][ci][k] = (gci < Ci && gco < Co) ? w[((long)gco * Ci + gci) * 9 + t] : __float2bfloat16_rn(0.f);
         }
         __syncthreads();
-        if (q < P) {
 #pragma unroll
-            for (int t = 0; t < 9; ++t) {
-                const float* src = gz + nb[t] + c0;
-                for (int co = 0; co < nco; ++co) {
-                    const float g = src[co];
+        for (int t = 0; t < 9; ++t) {
+            const int k0 = c0 + 2 * tig, k1 = k0 + 8;
+            uint32_t a0h, a0l, a1h, a1l, a2h, a2l, a3h, a3l;
+            split_pair(gz, nb0[t], k0, Co, a0h, a0l);
+            split_pair(gz, nb1[t], k0, Co, a1h, a1l);
+            split_pair(gz, nb0[t], k1, Co, a2h, a2l);
+            split_pair(gz, nb1[t], k1, Co, a3h, a3l);
 #pragma unroll
-                    for (int c = 0; c < kCoTile; ++c) acc[c] = fmaf(g, ws[t][co][c], acc[c]);
-                }
+            for (int j = 0; j < 4; ++j) {
+                const bf16* row = &ws[t][j * 8 + gid][0];
+                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row + 2 * tig);
+                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 2 * tig + 8);
+                mma_bf16(acc[j], a0h, a1h, a2h, a3h, b0, b1);
+                mma_bf16(acc[j], a0l, a1l, a2l, a3l, b0, b1);
             }
         }
     }
-    if (q < P) {
 #pragma unroll
-        for (int c = 0; c < kCoTile; ++c)
-            if (ci0 + c < Ci) gin[q * Ci + ci0 + c] = acc[c];
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int ci = ci0 + j * 8 + 2 * tig + h;
+            if (ci >= Ci) continue;
+            if (q0 < P) gin[q0 * Ci + ci] = acc[j][h];
+            if (q1 < P) gin[q1 * Ci + ci] = acc[j][2 + h];
+        }
     }
 }
 
 // gw[co][ci][tap] += sum_p gz[p][co] in[nbr(p, tap)][ci]; gb[co] += sum_p gz[p][co]
-// blockDim = 256: thread (co_l, ci_l) = (tid / 16, tid % 16) of the block's tile.
-__global__ void k_conv_bwd_w(const float* __restrict__ gz, const bf16* __restrict__ in, float* __restrict__ gw,
-                             float* __restrict__ gb, long P, int lh, int lw, int Ci, int Co, long chunk) {
-    const int ci_tiles = (Ci + 15) / 16;
-    const int co = (blockIdx.x / ci_tiles) * 16 + threadIdx.x / 16;
-    const int ci = (blockIdx.x % ci_tiles) * 16 + threadIdx.x % 16;
+// on the tensor cores: per tap a GEMM with rows = output channels, columns =
+// input channels and the reduction over points.  A block owns 32 x 32
+// (output, input) channels, all 9 taps, and a chunk of points (a multiple of
+// kWgPts); partial sums go to the gradient by atomicAdd.  Per stage the
+// block stages, point-innermost, the gradient's 32 channels (split bf16
+// hi + lo as in k_conv_bwd_data) and the 9 neighbour rows of the input's 32
+// channels; warp w owns output rows 16 (w & 1) .. +15 and input columns
+// 16 (w >> 1) .. +15 for all 9 taps (72 FP32 accumulators a thread).
+constexpr int kWgPts = 32;               // points per shared-memory stage
+constexpr int kWgStr = kWgPts + 8;       // row stride (bf16): conflict-free fragment reads
+
+__global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz, const bf16* __restrict__ in,
+                                                    float* __restrict__ gw, float* __restrict__ gb, long P, int lh,
+                                                    int lw, int Ci, int Co, long chunk) {
+    __shared__ __align__(16) bf16 ah[kMmaCo][kWgStr], al[kMmaCo][kWgStr];   // [co][point]
+    __shared__ __align__(16) bf16 bs[9][kMmaCo][kWgStr];                    // [tap][ci][point]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int ci_tiles = (Ci + kMmaCo - 1) / kMmaCo;
+    const int co0 = (blockIdx.x / ci_tiles) * kMmaCo, ci0 = (blockIdx.x % ci_tiles) * kMmaCo;
     const long p0 = blockIdx.y * chunk, p1 = min(P, p0 + chunk);
-    if (co >= Co || ci >= Ci) return;
-    float acc[9], accb = 0.f;
+    const int mrow = (warp & 1) * 16, ncol = (warp >> 1) * 16;
+    // staging roles: the gradient's channel is fixed per thread (128 % 32 == 0)
+    const int sco = threadIdx.x % kMmaCo;
+    const bool do_b = (ci0 == 0) && (co0 + sco < Co);
+    float accb = 0.f;
+    float acc[9][2][4];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) acc[t] = 0.f;
-    const bool do_b = (ci == 0);
-    for (long p = p0; p < p1; ++p) {
-        const float g = gz[p * Co + co];
-        if (do_b) accb += g;
+    for (int t = 0; t < 9; ++t)
 #pragma unroll
-        for (int t = 0; t < 9; ++t)
-            acc[t] = fmaf(g, __bfloat162float(in[nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci]), acc[t]);
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[t][j][r] = 0.f;
+    for (long ps = p0; ps < p1; ps += kWgPts) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < kMmaCo * kWgPts; e += blockDim.x) {
+            const int k = e / kMmaCo;
+            const long p = ps + k;
+            float g = 0.f;
+            if (p < p1 && co0 + sco < Co) g = gz[p * Co + co0 + sco];
+            accb += g;
+            const bf16 hi = __float2bfloat16_rn(g);
+            ah[sco][k] = hi;
+            al[sco][k] = __float2bfloat16_rn(g - __bfloat162float(hi));
+        }
+        for (int e = threadIdx.x; e < 9 * kMmaCo * kWgPts; e += blockDim.x) {
+            const int c = e % kMmaCo, k = (e / kMmaCo) % kWgPts, t = e / (kMmaCo * kWgPts);
+            const long p = ps + k;
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (p < p1 && ci0 + c < Ci) v = in[nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci0 + c];
+            bs[t][c][k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k0 = 0; k0 < kWgPts; k0 += kMmaK) {
+            const int kc = k0 + 2 * tig;
+            const uint32_t h0 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid][kc]);
+            const uint32_t h1 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid + 8][kc]);
+            const uint32_t h2 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid][kc + 8]);
+            const uint32_t h3 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid + 8][kc + 8]);
+            const uint32_t l0 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid][kc]);
+            const uint32_t l1 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid + 8][kc]);
+            const uint32_t l2 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid][kc + 8]);
+            const uint32_t l3 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid + 8][kc + 8]);
+#pragma unroll
+            for (int t = 0; t < 9; ++t) {
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const bf16* row = &bs[t][ncol + j * 8 + gid][0];
+                    const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row + kc);
+                    const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + kc + 8);
+                    mma_bf16(acc[t][j], h0, h1, h2, h3, b0, b1);
+                    mma_bf16(acc[t][j], l0, l1, l2, l3, b0, b1);
+                }
+            }
+        }
     }
 #pragma unroll
-    for (int t = 0; t < 9; ++t) atomicAdd(&gw[((long)co * Ci + ci) * 9 + t], acc[t]);
-    if (do_b) atomicAdd(&gb[co], accb);
+    for (int t = 0; t < 9; ++t) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int co = co0 + mrow + gid + (r >> 1) * 8;
+                const int ci = ci0 + ncol + j * 8 + 2 * tig + (r & 1);
+                if (co < Co && ci < Ci) atomicAdd(&gw[((long)co * Ci + ci) * 9 + t], acc[t][j][r]);
+            }
+        }
+    }
+    if (do_b) atomicAdd(&gb[co0 + sco], accb);
 }
 
 // x [B][C][H][W] FP32 -> [B][H][W][C] bfloat16
@@ -412,9 +559,9 @@ int dec_id(int l, int s) { return 2 * kLevels + 2 * (kLevels - 2 - l) + s; }
 int conv_fwd(nsstab_unet* n, int id, const bf16* in, int l, int B) {
     const ConvDesc& d = n->conv[id];
     const long P = (long)B * n->h(l) * n->w(l);
-    const dim3 g((unsigned)((P + kFwdThreads - 1) / kFwdThreads), (unsigned)((d.co + kCoTile - 1) / kCoTile));
-    k_conv_fwd<<<g, kFwdThreads, 0, n->stream>>>(in, n->wq + d.w_off, n->theta + d.b_off, n->act[id], P, n->lh - l,
-                                                  n->lw - l, d.ci, d.co);
+    const dim3 g((unsigned)((P + kMmaPix - 1) / kMmaPix), (unsigned)((d.co + kMmaCo - 1) / kMmaCo));
+    k_conv_fwd<<<g, 128, 0, n->stream>>>(in, n->wq + d.w_off, n->theta + d.b_off, n->act[id], P, n->lh - l,
+                                         n->lw - l, d.ci, d.co);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
@@ -426,15 +573,17 @@ int conv_bwd(nsstab_unet* n, int id, const bf16* in, float* g, float* gin, int l
     const long P = (long)B * n->h(l) * n->w(l);
     k_relu_mask<<<grid_for(P * d.co, 256), 256, 0, n->stream>>>(g, n->act[id], P * d.co);
     NS_LAUNCH_CHECK();
-    const long chunk = std::max<long>(64, (P + 255) / 256);
-    const dim3 gw((unsigned)(((d.co + 15) / 16) * ((d.ci + 15) / 16)), (unsigned)((P + chunk - 1) / chunk));
-    k_conv_bwd_w<<<gw, 256, 0, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P, n->lh - l, n->lw - l,
+    // about two blocks per SM in all, each chunk a whole number of stages
+    const long tiles = (long)((d.co + kMmaCo - 1) / kMmaCo) * ((d.ci + kMmaCo - 1) / kMmaCo);
+    const long nchunk = std::max<long>(1, 2 * 152 / tiles);
+    const long chunk = std::max<long>(4 * kWgPts, ((P + nchunk - 1) / nchunk + kWgPts - 1) / kWgPts * kWgPts);
+    const dim3 gw((unsigned)tiles, (unsigned)((P + chunk - 1) / chunk));
+    k_conv_bwd_w<<<gw, 128, 0, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P, n->lh - l, n->lw - l,
                                             d.ci, d.co, chunk);
     NS_LAUNCH_CHECK();
     if (gin) {
-        const dim3 gd((unsigned)((P + kFwdThreads - 1) / kFwdThreads), (unsigned)((d.ci + kCoTile - 1) / kCoTile));
-        k_conv_bwd_data<<<gd, kFwdThreads, 0, n->stream>>>(g, n->wq + d.w_off, gin, P, n->lh - l, n->lw - l, d.ci,
-                                                           d.co);
+        const dim3 gd((unsigned)((P + kMmaPix - 1) / kMmaPix), (unsigned)((d.ci + kMmaCo - 1) / kMmaCo));
+        k_conv_bwd_data<<<gd, 128, 0, n->stream>>>(g, n->wq + d.w_off, gin, P, n->lh - l, n->lw - l, d.ci, d.co);
         NS_LAUNCH_CHECK();
     }
     return NSSTAB_OK;
