@@ -219,29 +219,110 @@ __global__ void __launch_bounds__(128) k_conv_bwd_data(const float* __restrict__
 // on the tensor cores: per tap a GEMM with rows = output channels, columns =
 // input channels and the reduction over points.  A block owns 32 x 32
 // (output, input) channels, all 9 taps, and a chunk of points (a multiple of
-// kWgPts); partial sums go to the gradient by atomicAdd.  Per stage the
-// block stages, point-innermost, the gradient's 32 channels (split bf16
-// hi + lo as in k_conv_bwd_data) and the 9 neighbour rows of the input's 32
-// channels; warp w owns output rows 16 (w & 1) .. +15 and input columns
-// 16 (w >> 1) .. +15 for all 9 taps (72 FP32 accumulators a thread).
-constexpr int kWgPts = 32;               // points per shared-memory stage
-constexpr int kWgStr = kWgPts + 8;       // row stride (bf16): conflict-free fragment reads
+// kWgPts); partial sums go to the gradient by atomicAdd.  Shared memory holds
+// two stages (double buffering), each point-major: the gradient's 32
+// channels split bf16 hi + lo as in k_conv_bwd_data, and the 9 neighbour
+// rows of the input's 32 channels (16-byte cp.async copies when VEC: input
+// channels a multiple of 8).  Fragments come from ldmatrix.trans; warp w
+// owns output rows 16 (w & 1) .. +15 and input columns 16 (w >> 1) .. +15
+// for all 9 taps (72 FP32 accumulators a thread).
+constexpr int kWgPts = 32;               // points per stage
+constexpr int kWgStr = kMmaCo + 8;       // row stride (bf16): 80 bytes, conflict-free ldmatrix
+struct WgStage {
+    bf16 ah[kWgPts][kWgStr], al[kWgPts][kWgStr];   // [point][co]
+    bf16 b[9][kWgPts][kWgStr];                     // [tap][point][ci]
+};
+constexpr int kWgSmem = 2 * (int)sizeof(WgStage);
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+// 16-byte global -> shared copy; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N));
+}
+
+// the input rows of one stage into st.b (asynchronous when VEC)
+template <bool VEC>
+__device__ __forceinline__ void wg_stage_in(WgStage& st, const bf16* __restrict__ in, long ps, long p1, int lh,
+                                            int lw, int Ci, int ci0) {
+    if (VEC) {
+        // thread: point k = tid / 4, channel group g = tid % 4, one copy per tap
+        const int k = threadIdx.x >> 2, g = threadIdx.x & 3;
+        const long p = ps + k;
+        const bool ok = (p < p1) && (ci0 + 8 * g < Ci);
+#pragma unroll
+        for (int t = 0; t < 9; ++t) {
+            const bf16* src = ok ? in + nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci0 + 8 * g : in;
+            cp_async16(smem_u32(&st.b[t][k][8 * g]), src, ok ? 16 : 0);
+        }
+    } else {
+#pragma unroll 8
+        for (int e = threadIdx.x; e < 9 * kWgPts * kMmaCo; e += 128) {
+            const int c = e % kMmaCo, k = (e / kMmaCo) % kWgPts, t = e / (kMmaCo * kWgPts);
+            const long p = ps + k;
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (p < p1 && ci0 + c < Ci) v = in[nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci0 + c];
+            st.b[t][k][c] = v;
+        }
+    }
+}
+
+// the gradient of one stage into registers: thread f = tid + 128 i (i = 0, 1)
+// holds point f / 8, channels co0 + 4 (f % 8) .. +3
+__device__ __forceinline__ void wg_load_gz(float (&v)[2][4], const float* __restrict__ gz, long ps, long p1,
+                                           int Co, int co0) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int f = threadIdx.x + 128 * i;
+        const long p = ps + (f >> 3);
+        const int c = co0 + 4 * (f & 7);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[i][u] = (p < p1 && c + u < Co) ? gz[p * Co + c + u] : 0.f;
+    }
+}
+
+__device__ __forceinline__ void wg_store_gz(WgStage& st, const float (&v)[2][4], float (&accb)[4]) {
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int f = threadIdx.x + 128 * i;
+        bf16 h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            accb[u] += v[i][u];
+            h[u] = __float2bfloat16_rn(v[i][u]);
+            l[u] = __float2bfloat16_rn(v[i][u] - __bfloat162float(h[u]));
+        }
+        *reinterpret_cast<uint2*>(&st.ah[f >> 3][4 * (f & 7)]) = make_uint2(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]));
+        *reinterpret_cast<uint2*>(&st.al[f >> 3][4 * (f & 7)]) = make_uint2(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]));
+    }
+}
+
+template <bool VEC>
 __global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz, const bf16* __restrict__ in,
                                                     float* __restrict__ gw, float* __restrict__ gb, long P, int lh,
                                                     int lw, int Ci, int Co, long chunk) {
-    __shared__ __align__(16) bf16 ah[kMmaCo][kWgStr], al[kMmaCo][kWgStr];   // [co][point]
-    __shared__ __align__(16) bf16 bs[9][kMmaCo][kWgStr];                    // [tap][ci][point]
+    extern __shared__ __align__(16) unsigned char wg_smem[];
+    WgStage* st = reinterpret_cast<WgStage*>(wg_smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gid = lane >> 2, tig = lane & 3;
     const int ci_tiles = (Ci + kMmaCo - 1) / kMmaCo;
     const int co0 = (blockIdx.x / ci_tiles) * kMmaCo, ci0 = (blockIdx.x % ci_tiles) * kMmaCo;
     const long p0 = blockIdx.y * chunk, p1 = min(P, p0 + chunk);
     const int mrow = (warp & 1) * 16, ncol = (warp >> 1) * 16;
-    // staging roles: the gradient's channel is fixed per thread (128 % 32 == 0)
-    const int sco = threadIdx.x % kMmaCo;
-    const bool do_b = (ci0 == 0) && (co0 + sco < Co);
-    float accb = 0.f;
+    // ldmatrix row addresses: lane = 8 i + r supplies row r of 8x8 matrix i
+    const int lr = lane & 7, li = lane >> 3;
+    const int a_k = (li >> 1) * 8 + lr, a_m = mrow + (li & 1) * 8;   // A^T stored [point][co]
+    const int b_k = (li & 1) * 8 + lr, b_n = ncol + (li >> 1) * 8;   // B stored [point][ci]
     float acc[9][2][4];
 #pragma unroll
     for (int t = 0; t < 9; ++t)
@@ -249,50 +330,44 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[t][j][r] = 0.f;
-    for (long ps = p0; ps < p1; ps += kWgPts) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kMmaCo * kWgPts; e += blockDim.x) {
-            const int k = e / kMmaCo;
-            const long p = ps + k;
-            float g = 0.f;
-            if (p < p1 && co0 + sco < Co) g = gz[p * Co + co0 + sco];
-            accb += g;
-            const bf16 hi = __float2bfloat16_rn(g);
-            ah[sco][k] = hi;
-            al[sco][k] = __float2bfloat16_rn(g - __bfloat162float(hi));
-        }
-        for (int e = threadIdx.x; e < 9 * kMmaCo * kWgPts; e += blockDim.x) {
-            const int c = e % kMmaCo, k = (e / kMmaCo) % kWgPts, t = e / (kMmaCo * kWgPts);
-            const long p = ps + k;
-            bf16 v = __float2bfloat16_rn(0.f);
-            if (p < p1 && ci0 + c < Ci) v = in[nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci0 + c];
-            bs[t][c][k] = v;
+    float accb[4] = {0.f, 0.f, 0.f, 0.f};
+    float gv[2][4];
+    wg_stage_in<VEC>(st[0], in, p0, p1, lh, lw, Ci, ci0);
+    cp_async_commit();
+    wg_load_gz(gv, gz, p0, p1, Co, co0);
+    wg_store_gz(st[0], gv, accb);
+    int buf = 0;
+    for (long ps = p0; ps < p1; ps += kWgPts, buf ^= 1) {
+        const bool more = ps + kWgPts < p1;
+        if (more) {
+            wg_stage_in<VEC>(st[buf ^ 1], in, ps + kWgPts, p1, lh, lw, Ci, ci0);
+            cp_async_commit();
+            wg_load_gz(gv, gz, ps + kWgPts, p1, Co, co0);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
+        const WgStage& s = st[buf];
 #pragma unroll
         for (int k0 = 0; k0 < kWgPts; k0 += kMmaK) {
-            const int kc = k0 + 2 * tig;
-            const uint32_t h0 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid][kc]);
-            const uint32_t h1 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid + 8][kc]);
-            const uint32_t h2 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid][kc + 8]);
-            const uint32_t h3 = *reinterpret_cast<const uint32_t*>(&ah[mrow + gid + 8][kc + 8]);
-            const uint32_t l0 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid][kc]);
-            const uint32_t l1 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid + 8][kc]);
-            const uint32_t l2 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid][kc + 8]);
-            const uint32_t l3 = *reinterpret_cast<const uint32_t*>(&al[mrow + gid + 8][kc + 8]);
+            uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
+            ldsm_x4_t(smem_u32(&s.ah[k0 + a_k][a_m]), h0, h1, h2, h3);
+            ldsm_x4_t(smem_u32(&s.al[k0 + a_k][a_m]), l0, l1, l2, l3);
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const bf16* row = &bs[t][ncol + j * 8 + gid][0];
-                    const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row + kc);
-                    const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + kc + 8);
-                    mma_bf16(acc[t][j], h0, h1, h2, h3, b0, b1);
-                    mma_bf16(acc[t][j], l0, l1, l2, l3, b0, b1);
-                }
+                uint32_t b00, b01, b10, b11;
+                ldsm_x4_t(smem_u32(&s.b[t][k0 + b_k][b_n]), b00, b01, b10, b11);
+                mma_bf16(acc[t][0], h0, h1, h2, h3, b00, b01);
+                mma_bf16(acc[t][0], l0, l1, l2, l3, b00, b01);
+                mma_bf16(acc[t][1], h0, h1, h2, h3, b10, b11);
+                mma_bf16(acc[t][1], l0, l1, l2, l3, b10, b11);
             }
         }
+        if (more) wg_store_gz(st[buf ^ 1], gv, accb);
+        __syncthreads();
     }
+    const int gid = lane >> 2, tig = lane & 3;
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
 #pragma unroll
@@ -305,7 +380,12 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz
             }
         }
     }
-    if (do_b) atomicAdd(&gb[co0 + sco], accb);
+    if (ci0 == 0) {
+        const int c = co0 + 4 * (threadIdx.x & 7);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (c + u < Co) atomicAdd(&gb[c + u], accb[u]);
+    }
 }
 
 // x [B][C][H][W] FP32 -> [B][H][W][C] bfloat16
@@ -573,13 +653,18 @@ int conv_bwd(nsstab_unet* n, int id, const bf16* in, float* g, float* gin, int l
     const long P = (long)B * n->h(l) * n->w(l);
     k_relu_mask<<<grid_for(P * d.co, 256), 256, 0, n->stream>>>(g, n->act[id], P * d.co);
     NS_LAUNCH_CHECK();
-    // about two blocks per SM in all, each chunk a whole number of stages
+    // about three blocks per SM in all, each chunk a whole number of stages
     const long tiles = (long)((d.co + kMmaCo - 1) / kMmaCo) * ((d.ci + kMmaCo - 1) / kMmaCo);
-    const long nchunk = std::max<long>(1, 2 * 152 / tiles);
+    const long nchunk = std::max<long>(1, 3 * 152 / tiles);
     const long chunk = std::max<long>(4 * kWgPts, ((P + nchunk - 1) / nchunk + kWgPts - 1) / kWgPts * kWgPts);
     const dim3 gw((unsigned)tiles, (unsigned)((P + chunk - 1) / chunk));
-    k_conv_bwd_w<<<gw, 128, 0, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P, n->lh - l, n->lw - l,
-                                            d.ci, d.co, chunk);
+    const bool vec = d.ci % 8 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0;
+    if (vec)
+        k_conv_bwd_w<true><<<gw, 128, kWgSmem, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P,
+                                                             n->lh - l, n->lw - l, d.ci, d.co, chunk);
+    else
+        k_conv_bwd_w<false><<<gw, 128, kWgSmem, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P,
+                                                              n->lh - l, n->lw - l, d.ci, d.co, chunk);
     NS_LAUNCH_CHECK();
     if (gin) {
         const dim3 gd((unsigned)((P + kMmaPix - 1) / kMmaPix), (unsigned)((d.ci + kMmaCo - 1) / kMmaCo));
@@ -703,6 +788,13 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
         set_error("unet_create: need 1 <= in_ch <= 64, 1 <= width <= 256, max_batch >= 1, ny and nx powers of two "
                   ">= 8, max_batch*ny*nx <= 2^28");
         return NSSTAB_ERR_INVALID_ARG;
+    }
+    if (cudaFuncSetAttribute(k_conv_bwd_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_conv_bwd_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) !=
+            cudaSuccess) {
+        set_error("unet_create: cudaFuncSetAttribute failed");
+        return NSSTAB_ERR_CUDA;
     }
     nsstab_unet* n = new nsstab_unet();
     n->in_ch = in_ch;
