@@ -4,19 +4,18 @@
 // Storage: activations in bfloat16, channels innermost ([B][H][W][C]), so
 // the channels of one point are one contiguous run; weights as FP32 masters
 // (with Adam's moments) plus a bfloat16 copy that the convolutions read;
-// every sum in FP32; gradients of activations in FP32.
+// every sum in FP32; gradients of activations in FP32 (bfloat16 hi + lo
+// planes where a GEMM reads them).
 //
 // Kernels (one pass each, no im2col buffer):
-//   k_conv_fwd       3x3 periodic convolution + bias + ReLU on the tensor
-//                    cores: implicit GEMM in BF16 mma.sync steps with FP32
-//                    accumulation (64 points x 32 output channels a block)
-//   k_conv_bwd_data  gradient of the input on the tensor cores: the same
-//                    implicit GEMM with the channels exchanged and the taps
-//                    mirrored, the FP32 gradient split into bf16 hi + lo
-//   k_conv_bwd_w     gradient of the weights and bias on the tensor cores:
-//                    a block owns 32 x 32 (output, input) channels, all 9
-//                    taps and a chunk of points (split reduction, atomicAdd
-//                    into the FP32 gradient)
+//   k_conv_gemm<false>  3x3 periodic convolution + bias + ReLU: implicit GEMM
+//                       on the tensor cores (BF16 mma.sync, FP32 accumulate)
+//   k_conv_gemm<true>   gradient of the input: the same GEMM with the
+//                       channels exchanged and the taps mirrored
+//   k_conv_bwd_w        gradient of the weights and bias: per tap a GEMM
+//                       reduced over points, split over blocks, atomicAdd
+//                       into the FP32 gradient
+//   k_relu_split        gradient of a ReLU output as bfloat16 hi + lo planes
 //   pooling, upsampling with concatenation, their adjoints, the 1x1 output
 //   layer, the mean-squared loss and Adam are pointwise kernels.
 // The layer sequence and every rounding point follow the oracle's
@@ -24,6 +23,8 @@
 #include <cuda_bf16.h>
 
 #include <cmath>
+#include <cstdint>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -50,31 +51,28 @@ __device__ __forceinline__ long nbr(long p, int lh, int lw, int dy, int dx) {
     return (((b << lh) + ((y + dy) & (H - 1))) << lw) + ((x + dx) & (W - 1));
 }
 
-// out[p][co] = relu(bias[co] + sum_{tap, ci} w[co][ci][tap] in[nbr(p, tap)][ci])
-// on the tensor cores: an implicit GEMM (rows = points, columns = output
-// channels, reduction = 9 taps x input channels) in BF16 mma.sync m16n8k16
-// steps with FP32 accumulation.  A block of 4 warps owns 64 points x 32
-// output channels; each warp 16 points x 4 n-tiles of 8.  The A fragments
-// (the 16 input channels of a point's neighbour at one tap) are read from
-// global memory (L1/L2 resident); the weights of the block's 32 output
-// channels for a chunk of 16 input channels and all 9 taps are staged in
-// shared memory, rows padded so that the B-fragment loads of a warp hit 32
-// distinct banks.  Products of bfloat16 values are exact in FP32, so only
-// the order of the FP32 sums differs from a scalar loop.
-constexpr int kMmaPix = 64, kMmaCo = 32, kMmaK = 16, kMmaPad = 8;
-
-__device__ __forceinline__ uint32_t pack_bf16(bf16 lo, bf16 hi) {
-    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-// channels k, k+1 of the point at offset nb (nb < 0: no point), zero beyond Ci
-__device__ __forceinline__ uint32_t ld_a(const bf16* __restrict__ in, long nb, int k, int Ci) {
-    if (nb < 0) return 0u;
-    const bf16 z = __float2bfloat16_rn(0.f);
-    const bf16 lo = (k < Ci) ? in[nb + k] : z;
-    const bf16 hi = (k + 1 < Ci) ? in[nb + k + 1] : z;
-    return pack_bf16(lo, hi);
-}
+// ---------------------------------------------------------------------------
+// The three 3x3 convolutions are implicit GEMMs on the tensor cores (BF16
+// mma.sync m16n8k16, FP32 accumulation; products of bfloat16 values are
+// exact in FP32, so only the order of the FP32 sums differs from a scalar
+// loop).  Operands reach shared memory by 16-byte cp.async copies (VEC: all
+// channel counts multiples of 8 and 16-byte aligned bases; otherwise plain
+// loads), in a ring of pipeline stages, and reach the registers by ldmatrix.
+// Every tile row is padded to 40 bf16 (80 bytes), which makes the ldmatrix
+// reads of a warp hit 32 distinct banks.
+//
+// The FP32 gradient of a ReLU output enters as two bfloat16 planes
+// (hi = bf16(g), lo = bf16(g - hi), written by k_relu_split), two mma steps
+// per fragment: about 16 significant bits of every product, summed in FP32.
+//
+// The bfloat16 weight copy wt is tap-major, wt[tap][co][ci], so that a tile
+// of (output, input) channels of one tap is a set of contiguous rows for
+// either GEMM that reads it.
+// ---------------------------------------------------------------------------
+constexpr int kMmaCo = 32, kMmaK = 16;
+constexpr int kStr = 40;            // padded tile row (bf16)
+constexpr int kTilePts = 64;        // points per block in the forward and input-gradient GEMMs
+constexpr int kRing = 4;            // pipeline depth of those GEMMs
 
 __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
                                          uint32_t b1) {
@@ -84,158 +82,13 @@ __device__ __forceinline__ void mma_bf16(float* d, uint32_t a0, uint32_t a1, uin
                  : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(128) k_conv_fwd(const bf16* __restrict__ in, const bf16* __restrict__ w,
-                                                  const float* __restrict__ bias, bf16* __restrict__ out, long P,
-                                                  int lh, int lw, int Ci, int Co) {
-    __shared__ __align__(16) bf16 ws[9][kMmaCo][kMmaK + kMmaPad];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const long p0 = (long)blockIdx.x * kMmaPix + warp * 16 + gid;   // rows gid and gid + 8 of the warp's tile
-    const long p1 = p0 + 8;
-    const int co0 = blockIdx.y * kMmaCo;
-    long nb0[9], nb1[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        nb0[t] = (p0 < P) ? nbr(p0, lh, lw, t / 3 - 1, t % 3 - 1) * Ci : -1;
-        nb1[t] = (p1 < P) ? nbr(p1, lh, lw, t / 3 - 1, t % 3 - 1) * Ci : -1;
-    }
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
-    for (int c0 = 0; c0 < Ci; c0 += kMmaK) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < 9 * kMmaCo * kMmaK; e += blockDim.x) {
-            const int k = e % kMmaK, co = (e / kMmaK) % kMmaCo, t = e / (kMmaK * kMmaCo);
-            const int gco = co0 + co, gci = c0 + k;
-            ws[t][co][k] = (gco < Co && gci < Ci) ? w[((long)gco * Ci + gci) * 9 + t] : __float2bfloat16_rn(0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int k0 = c0 + 2 * tig, k1 = k0 + 8;
-            const uint32_t a0 = ld_a(in, nb0[t], k0, Ci), a1 = ld_a(in, nb1[t], k0, Ci);
-            const uint32_t a2 = ld_a(in, nb0[t], k1, Ci), a3 = ld_a(in, nb1[t], k1, Ci);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bf16* row = &ws[t][j * 8 + gid][0];
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row + 2 * tig);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 2 * tig + 8);
-                mma_bf16(acc[j], a0, a1, a2, a3, b0, b1);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int co = co0 + j * 8 + 2 * tig + h;
-            if (co >= Co) continue;
-            const float b = bias[co];
-            if (p0 < P) out[p0 * Co + co] = __float2bfloat16_rn(fmaxf(acc[j][h] + b, 0.f));
-            if (p1 < P) out[p1 * Co + co] = __float2bfloat16_rn(fmaxf(acc[j][2 + h] + b, 0.f));
-        }
-    }
-}
-
-// gin[q][ci] = sum_{tap, co} w[co][ci][tap] gz[q - tap offset][co], on the
-// tensor cores like k_conv_fwd (rows = points, columns = input channels,
-// reduction = taps x output channels).  The FP32 gradient enters the BF16
-// products split as hi + lo (hi = its bfloat16 rounding, lo = the bfloat16
-// rounding of the rest), two mma steps per fragment: about 16 significant
-// bits of every product, summed in FP32.
-__device__ __forceinline__ void split_pair(const float* __restrict__ g, long nb, int k, int Co, uint32_t& hi,
-                                           uint32_t& lo) {
-    float x = 0.f, y = 0.f;
-    if (nb >= 0) {
-        if (k < Co) x = g[nb + k];
-        if (k + 1 < Co) y = g[nb + k + 1];
-    }
-    const bf16 xh = __float2bfloat16_rn(x), yh = __float2bfloat16_rn(y);
-    hi = pack_bf16(xh, yh);
-    lo = pack_bf16(__float2bfloat16_rn(x - __bfloat162float(xh)), __float2bfloat16_rn(y - __bfloat162float(yh)));
-}
-
-__global__ void __launch_bounds__(128) k_conv_bwd_data(const float* __restrict__ gz, const bf16* __restrict__ w,
-                                                       float* __restrict__ gin, long P, int lh, int lw, int Ci,
-                                                       int Co) {
-    __shared__ __align__(16) bf16 ws[9][kMmaCo][kMmaK + kMmaPad];   // [tap][input channel][output channel]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int gid = lane >> 2, tig = lane & 3;
-    const long q0 = (long)blockIdx.x * kMmaPix + warp * 16 + gid;
-    const long q1 = q0 + 8;
-    const int ci0 = blockIdx.y * kMmaCo;
-    long nb0[9], nb1[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-        nb0[t] = (q0 < P) ? nbr(q0, lh, lw, 1 - t / 3, 1 - t % 3) * Co : -1;
-        nb1[t] = (q1 < P) ? nbr(q1, lh, lw, 1 - t / 3, 1 - t % 3) * Co : -1;
-    }
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
-    for (int c0 = 0; c0 < Co; c0 += kMmaK) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < 9 * kMmaCo * kMmaK; e += blockDim.x) {
-            const int k = e % kMmaK, ci = (e / kMmaK) % kMmaCo, t = e / (kMmaK * kMmaCo);
-            const int gci = ci0 + ci, gco = c0 + k;
-            ws[t][ci][k] = (gci < Ci && gco < Co) ? w[((long)gco * Ci + gci) * 9 + t] : __float2bfloat16_rn(0.f);
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const int k0 = c0 + 2 * tig, k1 = k0 + 8;
-            uint32_t a0h, a0l, a1h, a1l, a2h, a2l, a3h, a3l;
-            split_pair(gz, nb0[t], k0, Co, a0h, a0l);
-            split_pair(gz, nb1[t], k0, Co, a1h, a1l);
-            split_pair(gz, nb0[t], k1, Co, a2h, a2l);
-            split_pair(gz, nb1[t], k1, Co, a3h, a3l);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const bf16* row = &ws[t][j * 8 + gid][0];
-                const uint32_t b0 = *reinterpret_cast<const uint32_t*>(row + 2 * tig);
-                const uint32_t b1 = *reinterpret_cast<const uint32_t*>(row + 2 * tig + 8);
-                mma_bf16(acc[j], a0h, a1h, a2h, a3h, b0, b1);
-                mma_bf16(acc[j], a0l, a1l, a2l, a3l, b0, b1);
-            }
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int ci = ci0 + j * 8 + 2 * tig + h;
-            if (ci >= Ci) continue;
-            if (q0 < P) gin[q0 * Ci + ci] = acc[j][h];
-            if (q1 < P) gin[q1 * Ci + ci] = acc[j][2 + h];
-        }
-    }
-}
-
-// gw[co][ci][tap] += sum_p gz[p][co] in[nbr(p, tap)][ci]; gb[co] += sum_p gz[p][co]
-// on the tensor cores: per tap a GEMM with rows = output channels, columns =
-// input channels and the reduction over points.  A block owns 32 x 32
-// (output, input) channels, all 9 taps, and a chunk of points (a multiple of
-// kWgPts); partial sums go to the gradient by atomicAdd.  Shared memory holds
-// two stages (double buffering), each point-major: the gradient's 32
-// channels split bf16 hi + lo as in k_conv_bwd_data, and the 9 neighbour
-// rows of the input's 32 channels (16-byte cp.async copies when VEC: input
-// channels a multiple of 8).  Fragments come from ldmatrix.trans; warp w
-// owns output rows 16 (w & 1) .. +15 and input columns 16 (w >> 1) .. +15
-// for all 9 taps (72 FP32 accumulators a thread).
-constexpr int kWgPts = 32;               // points per stage
-constexpr int kWgStr = kMmaCo + 8;       // row stride (bf16): 80 bytes, conflict-free ldmatrix
-struct WgStage {
-    bf16 ah[kWgPts][kWgStr], al[kWgPts][kWgStr];   // [point][co]
-    bf16 b[9][kWgPts][kWgStr];                     // [tap][point][ci]
-};
-constexpr int kWgSmem = 2 * (int)sizeof(WgStage);
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
 }
 __device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
     asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
@@ -252,74 +105,185 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N));
 }
 
-// the input rows of one stage into st.b (asynchronous when VEC)
-template <bool VEC>
-__device__ __forceinline__ void wg_stage_in(WgStage& st, const bf16* __restrict__ in, long ps, long p1, int lh,
-                                            int lw, int Ci, int ci0) {
+// rows x 32 channels of a [row][C] bfloat16 array into a padded tile: row r
+// of the tile is src_row(r) (negative: zeros), channels c0 .. c0 + 31 (zeros
+// at and beyond C).  NT threads share the work.
+template <bool VEC, int ROWS, int NT, class RowFn>
+__device__ __forceinline__ void stage_rows(bf16 (*tile)[kStr], const bf16* __restrict__ base, int C, int c0,
+                                           RowFn src_row) {
     if (VEC) {
-        // thread: point k = tid / 4, channel group g = tid % 4, one copy per tap
-        const int k = threadIdx.x >> 2, g = threadIdx.x & 3;
-        const long p = ps + k;
-        const bool ok = (p < p1) && (ci0 + 8 * g < Ci);
 #pragma unroll
-        for (int t = 0; t < 9; ++t) {
-            const bf16* src = ok ? in + nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci0 + 8 * g : in;
-            cp_async16(smem_u32(&st.b[t][k][8 * g]), src, ok ? 16 : 0);
+        for (int i = 0; i < (ROWS * 4 + NT - 1) / NT; ++i) {
+            const int f = threadIdx.x + i * NT;
+            if (ROWS * 4 % NT != 0 && f >= ROWS * 4) break;
+            const int r = f >> 2, g = f & 3;
+            const long row = src_row(r);
+            const bool ok = row >= 0 && c0 + 8 * g < C;
+            cp_async16(smem_u32(&tile[r][8 * g]), ok ? base + row * C + c0 + 8 * g : base, ok ? 16 : 0);
         }
     } else {
-#pragma unroll 8
-        for (int e = threadIdx.x; e < 9 * kWgPts * kMmaCo; e += 128) {
-            const int c = e % kMmaCo, k = (e / kMmaCo) % kWgPts, t = e / (kMmaCo * kWgPts);
-            const long p = ps + k;
-            bf16 v = __float2bfloat16_rn(0.f);
-            if (p < p1 && ci0 + c < Ci) v = in[nbr(p, lh, lw, t / 3 - 1, t % 3 - 1) * Ci + ci0 + c];
-            st.b[t][k][c] = v;
+#pragma unroll 4
+        for (int i = 0; i < (ROWS * kMmaCo + NT - 1) / NT; ++i) {
+            const int f = threadIdx.x + i * NT;
+            if (ROWS * kMmaCo % NT != 0 && f >= ROWS * kMmaCo) break;
+            const int r = f / kMmaCo, c = f % kMmaCo;
+            const long row = src_row(r);
+            tile[r][c] = (row >= 0 && c0 + c < C) ? base[row * C + c0 + c] : __float2bfloat16_rn(0.f);
         }
     }
 }
 
-// the gradient of one stage into registers: thread f = tid + 128 i (i = 0, 1)
-// holds point f / 8, channels co0 + 4 (f % 8) .. +3
-__device__ __forceinline__ void wg_load_gz(float (&v)[2][4], const float* __restrict__ gz, long ps, long p1,
-                                           int Co, int co0) {
+// Forward (BWD = false): out[p][co] = relu(bias[co] + sum_{tap, ci}
+//   wt[tap][co][ci] in[nbr(p, tap)][ci]) in bfloat16; rows = points,
+//   columns = output channels, reduction = (tap, input channel).
+// Input gradient (BWD = true): gin[q][ci] = sum_{tap, co} wt[tap][co][ci]
+//   gz[q - tap offset][co] in FP32; rows = points, columns = input channels,
+//   reduction = (tap, output channel), A = the gradient's hi and lo planes.
+// A block of 4 warps owns 64 points x 32 columns (warp w: points 16 w .. +15,
+// all 32 columns); one pipeline stage is one tap and 32 reduction channels.
+template <bool BWD, bool VEC>
+__global__ void __launch_bounds__(128) k_conv_gemm(const bf16* __restrict__ a_hi, const bf16* __restrict__ a_lo,
+                                                   const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                                   void* __restrict__ out, long P, int lh, int lw, int Ci, int Co) {
+    constexpr int NP = BWD ? 2 : 1;   // A planes
+    struct Stage {
+        bf16 a[NP][kTilePts][kStr];
+        bf16 b[kMmaCo][kStr];   // forward: [co][ci]; input gradient: [co][ci] read transposed
+    };
+    extern __shared__ __align__(16) unsigned char smem[];
+    Stage* ring = reinterpret_cast<Stage*>(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Ck = BWD ? Co : Ci;   // reduction channels per tap
+    const int Cn = BWD ? Ci : Co;   // output columns
+    const long pb = (long)blockIdx.x * kTilePts;
+    const int n0 = blockIdx.y * kMmaCo;
+    const int nck = (Ck + kMmaCo - 1) / kMmaCo;
+    const int nst = 9 * nck;
+    auto issue = [&](int s) {
+        Stage& st = ring[s % kRing];
+        const int t = s % 9, kc = (s / 9) * kMmaCo;
+        const int dy = BWD ? 1 - t / 3 : t / 3 - 1, dx = BWD ? 1 - t % 3 : t % 3 - 1;
+        auto arow = [&](int r) -> long {
+            const long p = pb + r;
+            return p < P ? nbr(p, lh, lw, dy, dx) : -1;
+        };
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int f = threadIdx.x + 128 * i;
-        const long p = ps + (f >> 3);
-        const int c = co0 + 4 * (f & 7);
+        for (int h = 0; h < NP; ++h) stage_rows<VEC, kTilePts, 128>(st.a[h], h ? a_lo : a_hi, Ck, kc, arow);
+        if (BWD) {   // rows = output channels kc .. kc + 31 (reduction), columns = input channels
+            stage_rows<VEC, kMmaCo, 128>(st.b, wt + (long)t * Co * Ci, Ci, n0, [&](int r) -> long {
+                return kc + r < Co ? (long)(kc + r) : -1;
+            });
+        } else {     // rows = output channels n0 .. n0 + 31 (columns), columns = input channels
+            stage_rows<VEC, kMmaCo, 128>(st.b, wt + (long)t * Co * Ci, Ci, kc, [&](int r) -> long {
+                return n0 + r < Co ? (long)(n0 + r) : -1;
+            });
+        }
+    };
+    float acc[4][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[i][u] = (p < p1 && c + u < Co) ? gz[p * Co + c + u] : 0.f;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+    // ldmatrix: lane = 8 i + r supplies row r of 8x8 matrix i
+    const int lr = lane & 7, li = lane >> 3;
+    const int a_m = warp * 16 + (li & 1) * 8 + lr, a_k = (li >> 1) * 8;        // A [point][k]
+    const int bf_n = (li >> 1) * 8 + lr, bf_k = (li & 1) * 8;                  // forward B [n][k]
+    const int bb_k = (li & 1) * 8 + lr, bb_n = (li >> 1) * 8;                  // input-gradient B [k][n]
+#pragma unroll
+    for (int s = 0; s < kRing - 1; ++s) {
+        if (s < nst) issue(s);
+        cp_async_commit();
     }
+    for (int s = 0; s < nst; ++s) {
+        cp_async_wait<kRing - 2>();
+        __syncthreads();
+        if (s + kRing - 1 < nst) issue(s + kRing - 1);
+        cp_async_commit();
+        const Stage& st = ring[s % kRing];
+#pragma unroll
+        for (int k0 = 0; k0 < kMmaCo; k0 += kMmaK) {
+            uint32_t a[NP][4];
+#pragma unroll
+            for (int h = 0; h < NP; ++h) ldsm_x4(smem_u32(&st.a[h][a_m][k0 + a_k]), a[h][0], a[h][1], a[h][2], a[h][3]);
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                uint32_t b0, b1, b2, b3;
+                if (BWD)
+                    ldsm_x4_t(smem_u32(&st.b[k0 + bb_k][16 * jj + bb_n]), b0, b1, b2, b3);
+                else
+                    ldsm_x4(smem_u32(&st.b[16 * jj + bf_n][k0 + bf_k]), b0, b1, b2, b3);
+#pragma unroll
+                for (int h = 0; h < NP; ++h) {
+                    mma_bf16(acc[2 * jj], a[h][0], a[h][1], a[h][2], a[h][3], b0, b1);
+                    mma_bf16(acc[2 * jj + 1], a[h][0], a[h][1], a[h][2], a[h][3], b2, b3);
+                }
+            }
+        }
+    }
+    cp_async_wait<0>();
+    const int gid = lane >> 2, tig = lane & 3;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const long p = pb + warp * 16 + gid + (r >> 1) * 8;
+            const int n = n0 + j * 8 + 2 * tig + (r & 1);
+            if (p >= P || n >= Cn) continue;
+            if (BWD)
+                static_cast<float*>(out)[p * Cn + n] = acc[j][r];
+            else
+                static_cast<bf16*>(out)[p * Cn + n] = __float2bfloat16_rn(fmaxf(acc[j][r] + bias[n], 0.f));
+        }
+    }
+}
+template <bool BWD>
+constexpr int conv_gemm_smem() {
+    return kRing * ((BWD ? 2 : 1) * kTilePts * kStr + kMmaCo * kStr) * (int)sizeof(bf16);
 }
 
-__device__ __forceinline__ void wg_store_gz(WgStage& st, const float (&v)[2][4], float (&accb)[4]) {
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int f = threadIdx.x + 128 * i;
-        bf16 h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            accb[u] += v[i][u];
-            h[u] = __float2bfloat16_rn(v[i][u]);
-            l[u] = __float2bfloat16_rn(v[i][u] - __bfloat162float(h[u]));
-        }
-        *reinterpret_cast<uint2*>(&st.ah[f >> 3][4 * (f & 7)]) = make_uint2(pack_bf16(h[0], h[1]), pack_bf16(h[2], h[3]));
-        *reinterpret_cast<uint2*>(&st.al[f >> 3][4 * (f & 7)]) = make_uint2(pack_bf16(l[0], l[1]), pack_bf16(l[2], l[3]));
-    }
-}
+// gw[co][ci][tap] += sum_p gz[p][co] in[nbr(p, tap)][ci]; gb[co] += sum_p gz[p][co]
+// on the tensor cores: per tap a GEMM with rows = output channels, columns =
+// input channels and the reduction over points.  A block owns 32 x 32
+// (output, input) channels, all 9 taps, and a chunk of points (a multiple of
+// kWgPts); partial sums go to the gradient by atomicAdd.  A stage holds,
+// point-major, the gradient's hi and lo planes and the 9 neighbour rows of
+// the input; fragments of both come from ldmatrix.trans.  Warp w owns output
+// rows 16 (w & 1) .. +15 and input columns 16 (w >> 1) .. +15 for all 9 taps
+// (72 FP32 accumulators a thread).
+constexpr int kWgPts = 32;   // points per stage
+constexpr int kWgRing = 2;
+struct WgStage {
+    bf16 ah[kWgPts][kStr], al[kWgPts][kStr];   // [point][co]
+    bf16 b[9][kWgPts][kStr];                   // [tap][point][ci]
+};
+constexpr int kWgSmem = kWgRing * (int)sizeof(WgStage);
 
 template <bool VEC>
-__global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz, const bf16* __restrict__ in,
-                                                    float* __restrict__ gw, float* __restrict__ gb, long P, int lh,
-                                                    int lw, int Ci, int Co, long chunk) {
-    extern __shared__ __align__(16) unsigned char wg_smem[];
-    WgStage* st = reinterpret_cast<WgStage*>(wg_smem);
+__global__ void __launch_bounds__(128) k_conv_bwd_w(const bf16* __restrict__ gzh, const bf16* __restrict__ gzl,
+                                                    const bf16* __restrict__ in, float* __restrict__ gw,
+                                                    float* __restrict__ gb, long P, int lh, int lw, int Ci, int Co,
+                                                    long chunk) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    WgStage* ring = reinterpret_cast<WgStage*>(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ci_tiles = (Ci + kMmaCo - 1) / kMmaCo;
     const int co0 = (blockIdx.x / ci_tiles) * kMmaCo, ci0 = (blockIdx.x % ci_tiles) * kMmaCo;
     const long p0 = blockIdx.y * chunk, p1 = min(P, p0 + chunk);
+    const int nst = (int)((p1 - p0 + kWgPts - 1) / kWgPts);
     const int mrow = (warp & 1) * 16, ncol = (warp >> 1) * 16;
-    // ldmatrix row addresses: lane = 8 i + r supplies row r of 8x8 matrix i
+    auto issue = [&](int s) {
+        WgStage& st = ring[s % kWgRing];
+        const long ps = p0 + (long)s * kWgPts;
+        auto prow = [&](int r) -> long { return ps + r < p1 ? ps + r : -1; };
+        stage_rows<VEC, kWgPts, 128>(st.ah, gzh, Co, co0, prow);
+        stage_rows<VEC, kWgPts, 128>(st.al, gzl, Co, co0, prow);
+#pragma unroll
+        for (int t = 0; t < 9; ++t)
+            stage_rows<VEC, kWgPts, 128>(st.b[t], in, Ci, ci0, [&](int r) -> long {
+                return ps + r < p1 ? nbr(ps + r, lh, lw, t / 3 - 1, t % 3 - 1) : -1;
+            });
+    };
+    // ldmatrix.trans row addresses: lane = 8 i + r supplies row r of matrix i
     const int lr = lane & 7, li = lane >> 3;
     const int a_k = (li >> 1) * 8 + lr, a_m = mrow + (li & 1) * 8;   // A^T stored [point][co]
     const int b_k = (li & 1) * 8 + lr, b_n = ncol + (li >> 1) * 8;   // B stored [point][ci]
@@ -330,43 +294,40 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int r = 0; r < 4; ++r) acc[t][j][r] = 0.f;
-    float accb[4] = {0.f, 0.f, 0.f, 0.f};
-    float gv[2][4];
-    wg_stage_in<VEC>(st[0], in, p0, p1, lh, lw, Ci, ci0);
-    cp_async_commit();
-    wg_load_gz(gv, gz, p0, p1, Co, co0);
-    wg_store_gz(st[0], gv, accb);
-    int buf = 0;
-    for (long ps = p0; ps < p1; ps += kWgPts, buf ^= 1) {
-        const bool more = ps + kWgPts < p1;
-        if (more) {
-            wg_stage_in<VEC>(st[buf ^ 1], in, ps + kWgPts, p1, lh, lw, Ci, ci0);
-            cp_async_commit();
-            wg_load_gz(gv, gz, ps + kWgPts, p1, Co, co0);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
+    float accb = 0.f;   // thread tid < 32 of a ci0 = 0 block: channel co0 + tid
+    const bool do_b = ci0 == 0 && threadIdx.x < kMmaCo && co0 + (int)threadIdx.x < Co;
+#pragma unroll
+    for (int s = 0; s < kWgRing - 1; ++s) {
+        if (s < nst) issue(s);
+        cp_async_commit();
+    }
+    for (int s = 0; s < nst; ++s) {
+        cp_async_wait<kWgRing - 2>();
         __syncthreads();
-        const WgStage& s = st[buf];
+        if (s + kWgRing - 1 < nst) issue(s + kWgRing - 1);
+        cp_async_commit();
+        const WgStage& st = ring[s % kWgRing];
+        if (do_b)
+#pragma unroll 8
+            for (int k = 0; k < kWgPts; ++k)
+                accb += __bfloat162float(st.ah[k][threadIdx.x]) + __bfloat162float(st.al[k][threadIdx.x]);
 #pragma unroll
         for (int k0 = 0; k0 < kWgPts; k0 += kMmaK) {
             uint32_t h0, h1, h2, h3, l0, l1, l2, l3;
-            ldsm_x4_t(smem_u32(&s.ah[k0 + a_k][a_m]), h0, h1, h2, h3);
-            ldsm_x4_t(smem_u32(&s.al[k0 + a_k][a_m]), l0, l1, l2, l3);
+            ldsm_x4_t(smem_u32(&st.ah[k0 + a_k][a_m]), h0, h1, h2, h3);
+            ldsm_x4_t(smem_u32(&st.al[k0 + a_k][a_m]), l0, l1, l2, l3);
 #pragma unroll
             for (int t = 0; t < 9; ++t) {
                 uint32_t b00, b01, b10, b11;
-                ldsm_x4_t(smem_u32(&s.b[t][k0 + b_k][b_n]), b00, b01, b10, b11);
+                ldsm_x4_t(smem_u32(&st.b[t][k0 + b_k][b_n]), b00, b01, b10, b11);
                 mma_bf16(acc[t][0], h0, h1, h2, h3, b00, b01);
                 mma_bf16(acc[t][0], l0, l1, l2, l3, b00, b01);
                 mma_bf16(acc[t][1], h0, h1, h2, h3, b10, b11);
                 mma_bf16(acc[t][1], l0, l1, l2, l3, b10, b11);
             }
         }
-        if (more) wg_store_gz(st[buf ^ 1], gv, accb);
-        __syncthreads();
     }
+    cp_async_wait<0>();
     const int gid = lane >> 2, tig = lane & 3;
 #pragma unroll
     for (int t = 0; t < 9; ++t) {
@@ -380,12 +341,7 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w(const float* __restrict__ gz
             }
         }
     }
-    if (ci0 == 0) {
-        const int c = co0 + 4 * (threadIdx.x & 7);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (c + u < Co) atomicAdd(&gb[c + u], accb[u]);
-    }
+    if (do_b) atomicAdd(&gb[co0 + threadIdx.x], accb);
 }
 
 // x [B][C][H][W] FP32 -> [B][H][W][C] bfloat16
@@ -473,9 +429,17 @@ __global__ void k_pool_bwd_add(const float* __restrict__ glow, const float* __re
 }
 
 // g *= (a > 0): the ReLU derivative from the stored activation
-__global__ void k_relu_mask(float* __restrict__ g, const bf16* __restrict__ a, long n) {
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
-        if (!(__bfloat162float(a[e]) > 0.f)) g[e] = 0.f;
+// gradient of a ReLU output as the two bfloat16 planes the convolution
+// GEMMs read: v = g where the activation is positive, else 0; hi = bf16(v),
+// lo = bf16(v - hi)
+__global__ void k_relu_split(const float* __restrict__ g, const bf16* __restrict__ a, bf16* __restrict__ hi,
+                             bf16* __restrict__ lo, long n) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float v = (__bfloat162float(a[e]) > 0.f) ? g[e] : 0.f;
+        const bf16 h = __float2bfloat16_rn(v);
+        hi[e] = h;
+        lo[e] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
 }
 
 // y[p] = b + sum_c w[c] h[p][c]
@@ -527,8 +491,30 @@ __global__ void k_out_bwd(const float* __restrict__ gy, const bf16* __restrict__
     }
 }
 
+// where the bfloat16 copy of flat parameter i lives: the 3x3 weights
+// [co][ci][tap] of each convolution tap-major as [tap][co][ci] at the same
+// offset; biases and the output layer in place
+struct WtMap {
+    int n = 0;
+    long off[16];
+    int ci[16], co[16];
+};
+__device__ __forceinline__ long wt_index(const WtMap& m, long i) {
+    for (int c = 0; c < m.n; ++c) {
+        const long j = i - m.off[c];
+        const long sz = 9L * m.ci[c] * m.co[c];
+        if (j >= 0 && j < sz) {
+            const int t = (int)(j % 9);
+            const long oc = j / 9;   // co * ci + ci_
+            return m.off[c] + (long)t * m.co[c] * m.ci[c] + oc;
+        }
+    }
+    return i;
+}
+
 __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
-                       bf16* __restrict__ wq, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+                       bf16* __restrict__ wt, WtMap map, long n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
         const float gi = g[i];
         const float mi = b1 * m[i] + (1.f - b1) * gi;
@@ -537,13 +523,13 @@ __global__ void k_adam(float* __restrict__ th, const float* __restrict__ g, floa
         v[i] = vi;
         const float t = th[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
         th[i] = t;
-        wq[i] = __float2bfloat16_rn(t);
+        wt[wt_index(map, i)] = __float2bfloat16_rn(t);
     }
 }
 
-__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ out, long n) {
+__global__ void k_to_bf16(const float* __restrict__ a, bf16* __restrict__ wt, WtMap map, long n) {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16_rn(a[i]);
+        wt[wt_index(map, i)] = __float2bfloat16_rn(a[i]);
 }
 
 unsigned grid_for(long n, int threads) {
@@ -564,7 +550,9 @@ struct nsstab_unet {
     std::vector<ConvDesc> conv;   // 14 convolutions in forward order, then the output layer
     std::vector<void*> allocs;
     float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
-    bf16* wq = nullptr;
+    bf16* wt = nullptr;           // bfloat16 weights, 3x3 convolutions tap-major
+    WtMap map;
+    bf16 *gzh = nullptr, *gzl = nullptr;   // a ReLU output's gradient as bf16 hi + lo planes
     bf16* x = nullptr;
     bf16* act[14] = {};           // ReLU outputs of the 14 convolutions
     bf16* pool[kLevels - 1] = {};
@@ -636,39 +624,49 @@ std::vector<ConvDesc> make_layout(int in_ch, int width, long* count) {
 int enc_id(int l, int s) { return 2 * l + s; }
 int dec_id(int l, int s) { return 2 * kLevels + 2 * (kLevels - 2 - l) + s; }
 
+// the 16-byte copy path of the GEMMs: channel counts multiples of 8 and
+// every base 16-byte aligned
+bool vec_ok(const ConvDesc& d, std::initializer_list<const void*> bases) {
+    if (d.ci % 8 || d.co % 8 || d.w_off % 8) return false;
+    for (const void* b : bases)
+        if (reinterpret_cast<uintptr_t>(b) % 16) return false;
+    return true;
+}
+
 int conv_fwd(nsstab_unet* n, int id, const bf16* in, int l, int B) {
     const ConvDesc& d = n->conv[id];
     const long P = (long)B * n->h(l) * n->w(l);
-    const dim3 g((unsigned)((P + kMmaPix - 1) / kMmaPix), (unsigned)((d.co + kMmaCo - 1) / kMmaCo));
-    k_conv_fwd<<<g, 128, 0, n->stream>>>(in, n->wq + d.w_off, n->theta + d.b_off, n->act[id], P, n->lh - l,
-                                         n->lw - l, d.ci, d.co);
+    const dim3 g((unsigned)((P + kTilePts - 1) / kTilePts), (unsigned)((d.co + kMmaCo - 1) / kMmaCo));
+    const bf16* w = n->wt + d.w_off;
+    auto k = vec_ok(d, {in, w}) ? k_conv_gemm<false, true> : k_conv_gemm<false, false>;
+    k<<<g, 128, conv_gemm_smem<false>(), n->stream>>>(in, nullptr, w, n->theta + d.b_off, n->act[id], P, n->lh - l,
+                                                      n->lw - l, d.ci, d.co);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
 
 // gradient g (of conv id's ReLU output) -> weight/bias gradients and, when
 // gin is not null, the gradient of the conv's input
-int conv_bwd(nsstab_unet* n, int id, const bf16* in, float* g, float* gin, int l, int B) {
+int conv_bwd(nsstab_unet* n, int id, const bf16* in, const float* g, float* gin, int l, int B) {
     const ConvDesc& d = n->conv[id];
     const long P = (long)B * n->h(l) * n->w(l);
-    k_relu_mask<<<grid_for(P * d.co, 256), 256, 0, n->stream>>>(g, n->act[id], P * d.co);
+    k_relu_split<<<grid_for(P * d.co, 256), 256, 0, n->stream>>>(g, n->act[id], n->gzh, n->gzl, P * d.co);
     NS_LAUNCH_CHECK();
     // about three blocks per SM in all, each chunk a whole number of stages
     const long tiles = (long)((d.co + kMmaCo - 1) / kMmaCo) * ((d.ci + kMmaCo - 1) / kMmaCo);
     const long nchunk = std::max<long>(1, 3 * 152 / tiles);
     const long chunk = std::max<long>(4 * kWgPts, ((P + nchunk - 1) / nchunk + kWgPts - 1) / kWgPts * kWgPts);
     const dim3 gw((unsigned)tiles, (unsigned)((P + chunk - 1) / chunk));
-    const bool vec = d.ci % 8 == 0 && reinterpret_cast<uintptr_t>(in) % 16 == 0;
-    if (vec)
-        k_conv_bwd_w<true><<<gw, 128, kWgSmem, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P,
-                                                             n->lh - l, n->lw - l, d.ci, d.co, chunk);
-    else
-        k_conv_bwd_w<false><<<gw, 128, kWgSmem, n->stream>>>(g, in, n->grad + d.w_off, n->grad + d.b_off, P,
-                                                              n->lh - l, n->lw - l, d.ci, d.co, chunk);
+    auto kw = vec_ok(d, {in, n->gzh, n->gzl}) ? k_conv_bwd_w<true> : k_conv_bwd_w<false>;
+    kw<<<gw, 128, kWgSmem, n->stream>>>(n->gzh, n->gzl, in, n->grad + d.w_off, n->grad + d.b_off, P, n->lh - l,
+                                        n->lw - l, d.ci, d.co, chunk);
     NS_LAUNCH_CHECK();
     if (gin) {
-        const dim3 gd((unsigned)((P + kMmaPix - 1) / kMmaPix), (unsigned)((d.ci + kMmaCo - 1) / kMmaCo));
-        k_conv_bwd_data<<<gd, 128, 0, n->stream>>>(g, n->wq + d.w_off, gin, P, n->lh - l, n->lw - l, d.ci, d.co);
+        const dim3 gd((unsigned)((P + kTilePts - 1) / kTilePts), (unsigned)((d.ci + kMmaCo - 1) / kMmaCo));
+        const bf16* w = n->wt + d.w_off;
+        auto kd = vec_ok(d, {n->gzh, n->gzl, w}) ? k_conv_gemm<true, true> : k_conv_gemm<true, false>;
+        kd<<<gd, 128, conv_gemm_smem<true>(), n->stream>>>(n->gzh, n->gzl, w, nullptr, gin, P, n->lh - l, n->lw - l,
+                                                           d.ci, d.co);
         NS_LAUNCH_CHECK();
     }
     return NSSTAB_OK;
@@ -701,7 +699,7 @@ int forward(nsstab_unet* n, const float* x, int B) {
         h = n->act[dec_id(l, 1)];
     }
     const ConvDesc& o = n->conv.back();
-    k_out_fwd<<<grid_for(P0, 256), 256, 0, n->stream>>>(h, n->wq + o.w_off, n->theta + o.b_off, n->y, P0, n->c(0));
+    k_out_fwd<<<grid_for(P0, 256), 256, 0, n->stream>>>(h, n->wt + o.w_off, n->theta + o.b_off, n->y, P0, n->c(0));
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
@@ -714,7 +712,7 @@ int backward(nsstab_unet* n, const float* target, int B, double* loss) {
     NS_CUDA(cudaMemcpyAsync(n->partial_host, n->partial, kRedBlocksU * sizeof(double), cudaMemcpyDeviceToHost,
                             n->stream));
     const ConvDesc& o = n->conv.back();
-    k_out_bwd<<<(unsigned)((P0 + 255) / 256), 256, 0, n->stream>>>(n->gy, n->act[dec_id(0, 1)], n->wq + o.w_off, n->g0,
+    k_out_bwd<<<(unsigned)((P0 + 255) / 256), 256, 0, n->stream>>>(n->gy, n->act[dec_id(0, 1)], n->wt + o.w_off, n->g0,
                                                                    n->grad + o.w_off, n->grad + o.b_off, P0, n->c(0));
     NS_LAUNCH_CHECK();
     float* g = n->g0;      // gradient of the current layer's output
@@ -789,10 +787,15 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
                   ">= 8, max_batch*ny*nx <= 2^28");
         return NSSTAB_ERR_INVALID_ARG;
     }
-    if (cudaFuncSetAttribute(k_conv_bwd_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_conv_bwd_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) !=
-            cudaSuccess) {
+    const bool attr_ok =
+        cudaFuncSetAttribute(k_conv_bwd_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) == cudaSuccess &&
+        cudaFuncSetAttribute(k_conv_bwd_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_conv_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             conv_gemm_smem<true>()) == cudaSuccess &&
+        cudaFuncSetAttribute(k_conv_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             conv_gemm_smem<true>()) == cudaSuccess;
+    if (!attr_ok) {
         set_error("unet_create: cudaFuncSetAttribute failed");
         return NSSTAB_ERR_CUDA;
     }
@@ -806,6 +809,13 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
     n->maxB = max_batch;
     n->stream = (cudaStream_t)stream;
     n->conv = make_layout(in_ch, width, &n->count);
+    for (const ConvDesc& d : n->conv)
+        if (d.k == 3) {
+            n->map.off[n->map.n] = d.w_off;
+            n->map.ci[n->map.n] = d.ci;
+            n->map.co[n->map.n] = d.co;
+            ++n->map.n;
+        }
     const long B = max_batch;
     int rc = NSSTAB_OK;
     auto A = [&](int r) {
@@ -815,7 +825,7 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
     A(n->alloc(&n->grad, n->count));
     A(n->alloc(&n->m, n->count));
     A(n->alloc(&n->v, n->count));
-    A(n->alloc(&n->wq, n->count));
+    A(n->alloc(&n->wt, n->count));
     A(n->alloc(&n->x, B * ny * nx * in_ch));
     for (int l = 0; l < kLevels; ++l) {
         const long P = B * n->h(l) * n->w(l);
@@ -835,6 +845,8 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
         gmax = std::max(gmax, P * (n->c(l) + (l + 1 < kLevels ? n->c(l + 1) : 0)));
         gmax = std::max(gmax, P * (long)(l == 0 ? std::max(in_ch, n->c(0)) : n->c(l - 1)));
     }
+    A(n->alloc(&n->gzh, gmax));
+    A(n->alloc(&n->gzl, gmax));
     A(n->alloc(&n->g0, gmax));
     A(n->alloc(&n->g1, gmax));
     A(n->alloc(&n->glow, gmax));
@@ -848,7 +860,7 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
     for (void* z : {(void*)n->theta, (void*)n->m, (void*)n->v})
         if (rc == NSSTAB_OK && cudaMemsetAsync(z, 0, n->count * sizeof(float), n->stream) != cudaSuccess)
             rc = NSSTAB_ERR_CUDA;
-    if (rc == NSSTAB_OK && cudaMemsetAsync(n->wq, 0, n->count * sizeof(bf16), n->stream) != cudaSuccess)
+    if (rc == NSSTAB_OK && cudaMemsetAsync(n->wt, 0, n->count * sizeof(bf16), n->stream) != cudaSuccess)
         rc = NSSTAB_ERR_CUDA;
     if (rc != NSSTAB_OK) {
         delete n;
@@ -869,7 +881,7 @@ int unet_set_params(nsstab_unet* net, const float* theta) {
     NS_CUDA(cudaMemsetAsync(net->m, 0, net->count * sizeof(float), net->stream));
     NS_CUDA(cudaMemsetAsync(net->v, 0, net->count * sizeof(float), net->stream));
     net->step = 0;
-    k_to_bf16<<<grid_for(net->count, 256), 256, 0, net->stream>>>(net->theta, net->wq, net->count);
+    k_to_bf16<<<grid_for(net->count, 256), 256, 0, net->stream>>>(net->theta, net->wt, net->map, net->count);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
@@ -915,7 +927,7 @@ int unet_train_step(nsstab_unet* net, const float* x, const float* target, int b
     NS_TRY(backward(net, target, batch, loss));
     net->step += 1;
     const float c1 = 1.f - std::pow(beta1, (float)net->step), c2 = 1.f - std::pow(beta2, (float)net->step);
-    k_adam<<<grid_for(net->count, 256), 256, 0, net->stream>>>(net->theta, net->grad, net->m, net->v, net->wq,
+    k_adam<<<grid_for(net->count, 256), 256, 0, net->stream>>>(net->theta, net->grad, net->m, net->v, net->wt, net->map,
                                                                net->count, lr, beta1, beta2, eps, c1, c2);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
