@@ -105,11 +105,12 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N));
 }
 
-// rows x 32 channels of a [row][C] bfloat16 array into a padded tile: row r
-// of the tile is src_row(r) (negative: zeros), channels c0 .. c0 + 31 (zeros
-// at and beyond C).  NT threads share the work.
+// rows x 32 channels of a [row][LD] bfloat16 array (C channels used) into a
+// padded tile: row r of the tile is src_row(r) (negative: zeros), channels
+// c0 .. c0 + 31 (zeros at and beyond C; VEC copies whole 8-channel groups,
+// so channels C .. LD - 1 must hold zeros).  NT threads share the work.
 template <bool VEC, int ROWS, int NT, class RowFn>
-__device__ __forceinline__ void stage_rows(bf16 (*tile)[kStr], const bf16* __restrict__ base, int C, int c0,
+__device__ __forceinline__ void stage_rows(bf16 (*tile)[kStr], const bf16* __restrict__ base, int C, int LD, int c0,
                                            RowFn src_row) {
     if (VEC) {
 #pragma unroll
@@ -119,7 +120,7 @@ __device__ __forceinline__ void stage_rows(bf16 (*tile)[kStr], const bf16* __res
             const int r = f >> 2, g = f & 3;
             const long row = src_row(r);
             const bool ok = row >= 0 && c0 + 8 * g < C;
-            cp_async16(smem_u32(&tile[r][8 * g]), ok ? base + row * C + c0 + 8 * g : base, ok ? 16 : 0);
+            cp_async16(smem_u32(&tile[r][8 * g]), ok ? base + row * LD + c0 + 8 * g : base, ok ? 16 : 0);
         }
     } else {
 #pragma unroll 4
@@ -128,7 +129,7 @@ __device__ __forceinline__ void stage_rows(bf16 (*tile)[kStr], const bf16* __res
             if (ROWS * kMmaCo % NT != 0 && f >= ROWS * kMmaCo) break;
             const int r = f / kMmaCo, c = f % kMmaCo;
             const long row = src_row(r);
-            tile[r][c] = (row >= 0 && c0 + c < C) ? base[row * C + c0 + c] : __float2bfloat16_rn(0.f);
+            tile[r][c] = (row >= 0 && c0 + c < C) ? base[row * LD + c0 + c] : __float2bfloat16_rn(0.f);
         }
     }
 }
@@ -141,10 +142,12 @@ __device__ __forceinline__ void stage_rows(bf16 (*tile)[kStr], const bf16* __res
 //   reduction = (tap, output channel), A = the gradient's hi and lo planes.
 // A block of 4 warps owns 64 points x 32 columns (warp w: points 16 w .. +15,
 // all 32 columns); one pipeline stage is one tap and 32 reduction channels.
-template <bool BWD, bool VEC>
+// VA / VB: 16-byte copies for the A rows (row stride lda) / the weight rows.
+template <bool BWD, bool VA, bool VB>
 __global__ void __launch_bounds__(128) k_conv_gemm(const bf16* __restrict__ a_hi, const bf16* __restrict__ a_lo,
                                                    const bf16* __restrict__ wt, const float* __restrict__ bias,
-                                                   void* __restrict__ out, long P, int lh, int lw, int Ci, int Co) {
+                                                   void* __restrict__ out, long P, int lh, int lw, int Ci, int Co,
+                                                   int lda) {
     constexpr int NP = BWD ? 2 : 1;   // A planes
     struct Stage {
         bf16 a[NP][kTilePts][kStr];
@@ -168,13 +171,13 @@ __global__ void __launch_bounds__(128) k_conv_gemm(const bf16* __restrict__ a_hi
             return p < P ? nbr(p, lh, lw, dy, dx) : -1;
         };
 #pragma unroll
-        for (int h = 0; h < NP; ++h) stage_rows<VEC, kTilePts, 128>(st.a[h], h ? a_lo : a_hi, Ck, kc, arow);
+        for (int h = 0; h < NP; ++h) stage_rows<VA, kTilePts, 128>(st.a[h], h ? a_lo : a_hi, Ck, lda, kc, arow);
         if (BWD) {   // rows = output channels kc .. kc + 31 (reduction), columns = input channels
-            stage_rows<VEC, kMmaCo, 128>(st.b, wt + (long)t * Co * Ci, Ci, n0, [&](int r) -> long {
+            stage_rows<VB, kMmaCo, 128>(st.b, wt + (long)t * Co * Ci, Ci, Ci, n0, [&](int r) -> long {
                 return kc + r < Co ? (long)(kc + r) : -1;
             });
         } else {     // rows = output channels n0 .. n0 + 31 (columns), columns = input channels
-            stage_rows<VEC, kMmaCo, 128>(st.b, wt + (long)t * Co * Ci, Ci, kc, [&](int r) -> long {
+            stage_rows<VB, kMmaCo, 128>(st.b, wt + (long)t * Co * Ci, Ci, Ci, kc, [&](int r) -> long {
                 return n0 + r < Co ? (long)(n0 + r) : -1;
             });
         }
@@ -249,7 +252,8 @@ constexpr int conv_gemm_smem() {
 // point-major, the gradient's hi and lo planes and the 9 neighbour rows of
 // the input; fragments of both come from ldmatrix.trans.  Warp w owns output
 // rows 16 (w & 1) .. +15 and input columns 16 (w >> 1) .. +15 for all 9 taps
-// (72 FP32 accumulators a thread).
+// (72 FP32 accumulators a thread).  VA / VB: 16-byte copies for the gradient
+// planes / the input rows (row stride ldin).
 constexpr int kWgPts = 32;   // points per stage
 constexpr int kWgRing = 2;
 struct WgStage {
@@ -258,11 +262,11 @@ struct WgStage {
 };
 constexpr int kWgSmem = kWgRing * (int)sizeof(WgStage);
 
-template <bool VEC>
+template <bool VA, bool VB>
 __global__ void __launch_bounds__(128) k_conv_bwd_w(const bf16* __restrict__ gzh, const bf16* __restrict__ gzl,
                                                     const bf16* __restrict__ in, float* __restrict__ gw,
                                                     float* __restrict__ gb, long P, int lh, int lw, int Ci, int Co,
-                                                    long chunk) {
+                                                    int ldin, long chunk) {
     extern __shared__ __align__(16) unsigned char smem[];
     WgStage* ring = reinterpret_cast<WgStage*>(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -275,11 +279,11 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w(const bf16* __restrict__ gzh
         WgStage& st = ring[s % kWgRing];
         const long ps = p0 + (long)s * kWgPts;
         auto prow = [&](int r) -> long { return ps + r < p1 ? ps + r : -1; };
-        stage_rows<VEC, kWgPts, 128>(st.ah, gzh, Co, co0, prow);
-        stage_rows<VEC, kWgPts, 128>(st.al, gzl, Co, co0, prow);
+        stage_rows<VA, kWgPts, 128>(st.ah, gzh, Co, Co, co0, prow);
+        stage_rows<VA, kWgPts, 128>(st.al, gzl, Co, Co, co0, prow);
 #pragma unroll
         for (int t = 0; t < 9; ++t)
-            stage_rows<VEC, kWgPts, 128>(st.b[t], in, Ci, ci0, [&](int r) -> long {
+            stage_rows<VB, kWgPts, 128>(st.b[t], in, Ci, ldin, ci0, [&](int r) -> long {
                 return ps + r < p1 ? nbr(ps + r, lh, lw, t / 3 - 1, t % 3 - 1) : -1;
             });
     };
@@ -344,13 +348,13 @@ __global__ void __launch_bounds__(128) k_conv_bwd_w(const bf16* __restrict__ gzh
     if (do_b) atomicAdd(&gb[co0 + threadIdx.x], accb);
 }
 
-// x [B][C][H][W] FP32 -> [B][H][W][C] bfloat16
-__global__ void k_to_nhwc(const float* __restrict__ x, bf16* __restrict__ out, long P, int HW, int C) {
-    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P * C; e += (long)gridDim.x * blockDim.x) {
-        const long p = e / C;
-        const int c = (int)(e % C);
+// x [B][C][H][W] FP32 -> [B][H][W][LD] bfloat16, channels C .. LD - 1 zero
+__global__ void k_to_nhwc(const float* __restrict__ x, bf16* __restrict__ out, long P, int HW, int C, int LD) {
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < P * LD; e += (long)gridDim.x * blockDim.x) {
+        const long p = e / LD;
+        const int c = (int)(e % LD);
         const long b = p / HW, s = p % HW;
-        out[e] = __float2bfloat16_rn(x[(b * C + c) * HW + s]);
+        out[e] = (c < C) ? __float2bfloat16_rn(x[(b * C + c) * HW + s]) : __float2bfloat16_rn(0.f);
     }
 }
 
@@ -544,6 +548,7 @@ using namespace nsstab;
 
 struct nsstab_unet {
     int in_ch = 0, width = 0, H = 0, W = 0, lh = 0, lw = 0, maxB = 0;
+    int ldx = 0;                  // channel stride of the bfloat16 input (in_ch rounded up to 8)
     cudaStream_t stream = nullptr;
     long count = 0;
     int step = 0;
@@ -624,49 +629,57 @@ std::vector<ConvDesc> make_layout(int in_ch, int width, long* count) {
 int enc_id(int l, int s) { return 2 * l + s; }
 int dec_id(int l, int s) { return 2 * kLevels + 2 * (kLevels - 2 - l) + s; }
 
-// the 16-byte copy path of the GEMMs: channel counts multiples of 8 and
-// every base 16-byte aligned
-bool vec_ok(const ConvDesc& d, std::initializer_list<const void*> bases) {
-    if (d.ci % 8 || d.co % 8 || d.w_off % 8) return false;
-    for (const void* b : bases)
-        if (reinterpret_cast<uintptr_t>(b) % 16) return false;
-    return true;
+bool al16(const void* p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+using GemmFn = void (*)(const bf16*, const bf16*, const bf16*, const float*, void*, long, int, int, int, int, int);
+using WgradFn = void (*)(const bf16*, const bf16*, const bf16*, float*, float*, long, int, int, int, int, int, long);
+template <bool BWD>
+GemmFn pick_gemm(bool va, bool vb) {
+    return va ? (vb ? k_conv_gemm<BWD, true, true> : k_conv_gemm<BWD, true, false>)
+              : (vb ? k_conv_gemm<BWD, false, true> : k_conv_gemm<BWD, false, false>);
+}
+WgradFn pick_wgrad(bool va, bool vb) {
+    return va ? (vb ? k_conv_bwd_w<true, true> : k_conv_bwd_w<true, false>)
+              : (vb ? k_conv_bwd_w<false, true> : k_conv_bwd_w<false, false>);
 }
 
-int conv_fwd(nsstab_unet* n, int id, const bf16* in, int l, int B) {
+// conv id on input rows `in` of stride lda (its input channels, or the
+// padded stride of the network input)
+int conv_fwd(nsstab_unet* n, int id, const bf16* in, int lda, int l, int B) {
     const ConvDesc& d = n->conv[id];
     const long P = (long)B * n->h(l) * n->w(l);
     const dim3 g((unsigned)((P + kTilePts - 1) / kTilePts), (unsigned)((d.co + kMmaCo - 1) / kMmaCo));
     const bf16* w = n->wt + d.w_off;
-    auto k = vec_ok(d, {in, w}) ? k_conv_gemm<false, true> : k_conv_gemm<false, false>;
+    const GemmFn k = pick_gemm<false>(lda % 8 == 0 && al16(in), d.ci % 8 == 0 && al16(w));
     k<<<g, 128, conv_gemm_smem<false>(), n->stream>>>(in, nullptr, w, n->theta + d.b_off, n->act[id], P, n->lh - l,
-                                                      n->lw - l, d.ci, d.co);
+                                                      n->lw - l, d.ci, d.co, lda);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }
 
 // gradient g (of conv id's ReLU output) -> weight/bias gradients and, when
-// gin is not null, the gradient of the conv's input
-int conv_bwd(nsstab_unet* n, int id, const bf16* in, const float* g, float* gin, int l, int B) {
+// gin is not null, the gradient of the conv's input (rows `in`, stride ldin)
+int conv_bwd(nsstab_unet* n, int id, const bf16* in, int ldin, const float* g, float* gin, int l, int B) {
     const ConvDesc& d = n->conv[id];
     const long P = (long)B * n->h(l) * n->w(l);
     k_relu_split<<<grid_for(P * d.co, 256), 256, 0, n->stream>>>(g, n->act[id], n->gzh, n->gzl, P * d.co);
     NS_LAUNCH_CHECK();
+    const bool vz = d.co % 8 == 0 && al16(n->gzh) && al16(n->gzl);
     // about three blocks per SM in all, each chunk a whole number of stages
     const long tiles = (long)((d.co + kMmaCo - 1) / kMmaCo) * ((d.ci + kMmaCo - 1) / kMmaCo);
     const long nchunk = std::max<long>(1, 3 * 152 / tiles);
     const long chunk = std::max<long>(4 * kWgPts, ((P + nchunk - 1) / nchunk + kWgPts - 1) / kWgPts * kWgPts);
     const dim3 gw((unsigned)tiles, (unsigned)((P + chunk - 1) / chunk));
-    auto kw = vec_ok(d, {in, n->gzh, n->gzl}) ? k_conv_bwd_w<true> : k_conv_bwd_w<false>;
+    const WgradFn kw = pick_wgrad(vz, ldin % 8 == 0 && al16(in));
     kw<<<gw, 128, kWgSmem, n->stream>>>(n->gzh, n->gzl, in, n->grad + d.w_off, n->grad + d.b_off, P, n->lh - l,
-                                        n->lw - l, d.ci, d.co, chunk);
+                                        n->lw - l, d.ci, d.co, ldin, chunk);
     NS_LAUNCH_CHECK();
     if (gin) {
         const dim3 gd((unsigned)((P + kTilePts - 1) / kTilePts), (unsigned)((d.ci + kMmaCo - 1) / kMmaCo));
         const bf16* w = n->wt + d.w_off;
-        auto kd = vec_ok(d, {n->gzh, n->gzl, w}) ? k_conv_gemm<true, true> : k_conv_gemm<true, false>;
+        const GemmFn kd = pick_gemm<true>(vz, d.ci % 8 == 0 && al16(w));
         kd<<<gd, 128, conv_gemm_smem<true>(), n->stream>>>(n->gzh, n->gzl, w, nullptr, gin, P, n->lh - l, n->lw - l,
-                                                           d.ci, d.co);
+                                                           d.ci, d.co, d.co);
         NS_LAUNCH_CHECK();
     }
     return NSSTAB_OK;
@@ -674,12 +687,12 @@ int conv_bwd(nsstab_unet* n, int id, const bf16* in, const float* g, float* gin,
 
 int forward(nsstab_unet* n, const float* x, int B) {
     const long P0 = (long)B * n->H * n->W;
-    k_to_nhwc<<<grid_for(P0 * n->in_ch, 256), 256, 0, n->stream>>>(x, n->x, P0, n->H * n->W, n->in_ch);
+    k_to_nhwc<<<grid_for(P0 * n->ldx, 256), 256, 0, n->stream>>>(x, n->x, P0, n->H * n->W, n->in_ch, n->ldx);
     NS_LAUNCH_CHECK();
     const bf16* h = n->x;
     for (int l = 0; l < kLevels; ++l) {
-        NS_TRY(conv_fwd(n, enc_id(l, 0), h, l, B));
-        NS_TRY(conv_fwd(n, enc_id(l, 1), n->act[enc_id(l, 0)], l, B));
+        NS_TRY(conv_fwd(n, enc_id(l, 0), h, l == 0 ? n->ldx : n->c(l - 1), l, B));
+        NS_TRY(conv_fwd(n, enc_id(l, 1), n->act[enc_id(l, 0)], n->c(l), l, B));
         h = n->act[enc_id(l, 1)];
         if (l < kLevels - 1) {
             const long Po = (long)B * n->h(l + 1) * n->w(l + 1);
@@ -694,8 +707,8 @@ int forward(nsstab_unet* n, const float* x, int B) {
         k_up_cat<<<grid_for(P * (n->c(l + 1) + n->c(l)), 256), 256, 0, n->stream>>>(
             h, n->act[enc_id(l, 1)], n->cat[l], P, n->h(l), n->w(l), n->c(l + 1), n->c(l));
         NS_LAUNCH_CHECK();
-        NS_TRY(conv_fwd(n, dec_id(l, 0), n->cat[l], l, B));
-        NS_TRY(conv_fwd(n, dec_id(l, 1), n->act[dec_id(l, 0)], l, B));
+        NS_TRY(conv_fwd(n, dec_id(l, 0), n->cat[l], n->c(l + 1) + n->c(l), l, B));
+        NS_TRY(conv_fwd(n, dec_id(l, 1), n->act[dec_id(l, 0)], n->c(l), l, B));
         h = n->act[dec_id(l, 1)];
     }
     const ConvDesc& o = n->conv.back();
@@ -718,9 +731,9 @@ int backward(nsstab_unet* n, const float* target, int B, double* loss) {
     float* g = n->g0;      // gradient of the current layer's output
     float* t = n->g1;      // its input's gradient
     for (int l = 0; l < kLevels - 1; ++l) {
-        NS_TRY(conv_bwd(n, dec_id(l, 1), n->act[dec_id(l, 0)], g, t, l, B));
+        NS_TRY(conv_bwd(n, dec_id(l, 1), n->act[dec_id(l, 0)], n->c(l), g, t, l, B));
         std::swap(g, t);
-        NS_TRY(conv_bwd(n, dec_id(l, 0), n->cat[l], g, t, l, B));
+        NS_TRY(conv_bwd(n, dec_id(l, 0), n->cat[l], n->c(l + 1) + n->c(l), g, t, l, B));
         std::swap(g, t);
         // g: gradient of cat[l]; split into the level below and the skip
         const long Pl = (long)B * n->h(l + 1) * n->w(l + 1);
@@ -738,10 +751,10 @@ int backward(nsstab_unet* n, const float* target, int B, double* loss) {
             NS_LAUNCH_CHECK();
             std::swap(g, t);
         }
-        NS_TRY(conv_bwd(n, enc_id(l, 1), n->act[enc_id(l, 0)], g, t, l, B));
+        NS_TRY(conv_bwd(n, enc_id(l, 1), n->act[enc_id(l, 0)], n->c(l), g, t, l, B));
         std::swap(g, t);
         const bf16* in = (l == 0) ? n->x : n->pool[l - 1];
-        NS_TRY(conv_bwd(n, enc_id(l, 0), in, g, l == 0 ? nullptr : t, l, B));
+        NS_TRY(conv_bwd(n, enc_id(l, 0), in, l == 0 ? n->ldx : n->c(l - 1), g, l == 0 ? nullptr : t, l, B));
         std::swap(g, t);
     }
     NS_CUDA(cudaStreamSynchronize(n->stream));
@@ -787,20 +800,22 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
                   ">= 8, max_batch*ny*nx <= 2^28");
         return NSSTAB_ERR_INVALID_ARG;
     }
-    const bool attr_ok =
-        cudaFuncSetAttribute(k_conv_bwd_w<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) == cudaSuccess &&
-        cudaFuncSetAttribute(k_conv_bwd_w<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kWgSmem) ==
-            cudaSuccess &&
-        cudaFuncSetAttribute(k_conv_gemm<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             conv_gemm_smem<true>()) == cudaSuccess &&
-        cudaFuncSetAttribute(k_conv_gemm<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             conv_gemm_smem<true>()) == cudaSuccess;
+    bool attr_ok = true;
+    for (int va = 0; va < 2; ++va)
+        for (int vb = 0; vb < 2; ++vb) {
+            attr_ok = attr_ok &&
+                      cudaFuncSetAttribute(pick_wgrad(va, vb), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           kWgSmem) == cudaSuccess &&
+                      cudaFuncSetAttribute(pick_gemm<true>(va, vb), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           conv_gemm_smem<true>()) == cudaSuccess;
+        }
     if (!attr_ok) {
         set_error("unet_create: cudaFuncSetAttribute failed");
         return NSSTAB_ERR_CUDA;
     }
     nsstab_unet* n = new nsstab_unet();
     n->in_ch = in_ch;
+    n->ldx = (in_ch + 7) / 8 * 8;
     n->width = width;
     n->H = ny;
     n->W = nx;
@@ -826,7 +841,7 @@ int unet_create(int in_ch, int width, int ny, int nx, int max_batch, void* strea
     A(n->alloc(&n->m, n->count));
     A(n->alloc(&n->v, n->count));
     A(n->alloc(&n->wt, n->count));
-    A(n->alloc(&n->x, B * ny * nx * in_ch));
+    A(n->alloc(&n->x, B * ny * nx * n->ldx));
     for (int l = 0; l < kLevels; ++l) {
         const long P = B * n->h(l) * n->w(l);
         A(n->alloc(&n->act[enc_id(l, 0)], P * n->c(l)));
