@@ -270,24 +270,32 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
                        double* eig_re, double* eig_im, double* resid, double* eigvecs,
                        int* n_eig, int* n_conv, int* n_matvec);
 
-/* Block Krylov-Schur: ONE eigenproblem of M = exp(T A) about the base flow,
- * built with a block of b vectors per product with M, so that every product
- * is one batched run of the step kernels over b fields (b times the
- * parallelism of arnoldi_eigs on the same grid).  Each new basis column is
- * orthogonalised by CGS2 against every column before it (Algorithm 1's
- * Gram-Schmidt step); the projected matrix is then banded with b
- * sub-diagonals, and the residual of a Ritz pair (mu, V y) is ||R y|| with
- * R the b rows below its square part.  The restart keeps the wanted Schur
- * vectors and the b residual columns (Sec. 3.2.2 with a rank-b instead of a
- * rank-1 remainder).  The paper's Algorithm 1 is the case b = 1.
- *   st:   a batch with ONE parameter set and b = per_set members
- *         (batch_create(cfg, 1, Re, D, b, ...)); b = 1 is a plain stepper
- *   base_omega: device [ny][nx] or NULL (current base)
- *   v0:   device [b][ny][nx], the start block (linearly independent)
- *   m:    basis size, 2 (nev + 1) + 2 b <= m <= 1024
- *   other arguments and outputs: as arnoldi_eigs (n_matvec counts single
- *   products, b per round).
- * Allocates about (2 m + 4 b) n doubles during the call.  Synchronous. */
+/* Block Krylov-Schur: an eigenproblem of M = exp(T A) about the base flow
+ * of each parameter set, built with a block of b vectors per product with M,
+ * so that every product is one batched run of the step kernels over b
+ * fields per set (b times the parallelism of arnoldi_eigs on the same
+ * grid).  Each new basis column is orthogonalised by CGS2 against every
+ * column before it (Algorithm 1's Gram-Schmidt step); the projected matrix
+ * is then banded with b sub-diagonals, and the residual of a Ritz pair
+ * (mu, V y) is ||R y|| with R the b rows below its square part.  The
+ * restart keeps the wanted Schur vectors and the b residual columns
+ * (Sec. 3.2.2 with a rank-b instead of a rank-1 remainder).  The paper's
+ * Algorithm 1 is the case b = 1.  The S parameter sets of a batch (a
+ * Reynolds or geometry sweep) are S independent block eigenproblems run in
+ * lockstep rounds: one batched product over all S b new columns, then one
+ * batched CGS2 across the sets per column; a set leaves the rounds when it
+ * has converged or used its restarts.
+ *   st:   a batch of S parameter sets and b = per_set members
+ *         (batch_create(cfg, S, Re, D, b, ...)); S = b = 1 is a plain stepper
+ *   base_omega: device [S][ny][nx] or NULL (current bases)
+ *   v0:   device [S][b][ny][nx], each set's start block (linearly independent)
+ *   m:    basis size per set, 2 (nev + 1) + 2 b <= m <= 1024
+ *   eig_re, eig_im, resid: host [S][nev+1]; eigvecs: device [S][nev+1][ny][nx]
+ *   or NULL; n_eig, n_conv, n_matvec: host [S] (n_matvec counts single
+ *   products, b per round).  With S = 1 these are the arrays of arnoldi_eigs.
+ * Allocates about S (m + 2 b) n + (m + 2 b) n doubles during the call.
+ * Returns NSSTAB_OK when every set converged, else NSSTAB_NOT_CONVERGED.
+ * Synchronous. */
 int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
                        int m, int nev, double tol, int max_restarts, double T,
                        double* eig_re, double* eig_im, double* resid, double* eigvecs,

@@ -301,178 +301,243 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
     return NSSTAB_OK;
 }
 
-// Block Krylov-Schur for ONE eigenproblem with a block of b = members
-// vectors per product with M (the batched stepper's members share one base
-// flow).  Column c of the basis is orthogonalised by CGS2 against all
-// columns before it, so M V_j = V_{j+b} B with B banded (b sub-diagonals);
-// the residual of a Ritz pair (theta, V y) is ||R y||, R the b rows of B
-// below the square part.  The restart keeps the wanted Schur vectors and
-// the b residual columns: M V_p = V_p T_p + V_res (R Z_p), the block form
-// of Sec. 3.2.2's decomposition (Eqs. 60-63 have b = 1).
-int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
-                      double tol, int max_restarts, int nsteps, ArnoldiOut& out) {
-    const double delta = 0.05;
-    const int b = st->members();
-    const int ncol = m + 2 * b;      // basis columns held
-    const int ldb = m + 2 * b;       // rows of the projected matrix
-    DevBuf Vd, tmp, Cd;
-    NS_CUDA(cudaMalloc(&Vd.p, (size_t)n * ncol * sizeof(double)));
-    NS_CUDA(cudaMalloc(&Cd.p, (size_t)ncol * ncol * sizeof(double)));
-    NS_CUDA(cudaMalloc(&tmp.p, (size_t)n * ncol * sizeof(double)));
-    double* V = Vd.p;
-    GsWork gs;
-    struct Release {
-        GsWork& g;
-        ~Release() { g.release(); }
-    } rel{gs};
-    std::vector<double> h(ncol), B((size_t)ldb * (m + b), 0.0);
-    // orthonormal start block
-    for (int i = 0; i < b; ++i) {
-        double* w = V + (size_t)i * n;
-        NS_CUDA(cudaMemcpyAsync(w, v0[i], n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-        double nrm = 0.0, beta = 0.0;
-        NS_TRY(vec_norm(w, n, &nrm, gs, stream));
-        NS_TRY(cgs2(V, n, n, i, w, h.data(), &beta, gs, stream));
-        if (!(nrm > 0.0) || !std::isfinite(nrm) || !(beta > 1e-10 * nrm)) {
-            set_error("block_arnoldi_eigs: start vectors are zero, non-finite or linearly dependent");
-            return NSSTAB_ERR_INVALID_ARG;
-        }
-        NS_TRY(vec_scale(w, w, n, 1.0 / beta, stream));
-    }
-    std::vector<const double*> in(b);
-    std::vector<double*> outp(b);
-    std::vector<double> T, Z;
+// Block Krylov-Schur with a block of b vectors per product with M, for
+// every parameter set of the batched stepper at once (b = members / sets;
+// the b members of a set share its base flow).  Column c of a basis is
+// orthogonalised by CGS2 against all columns before it, so
+// M V_j = V_{j+b} B with B banded (b sub-diagonals); the residual of a Ritz
+// pair (theta, V y) is ||R y||, R the b rows of B below the square part.
+// The restart keeps the wanted Schur vectors and the b residual columns:
+// M V_p = V_p T_p + V_res (R Z_p), the block form of Sec. 3.2.2's
+// decomposition (Eqs. 60-63 have b = 1).  The sets' processes advance in
+// lockstep rounds: one batched product with M over the b new columns of
+// every unfinished set, then for each of the b columns one batched CGS2
+// across the sets.  A finished set leaves the rounds.
+namespace {
+struct BlockProb {
+    double* V = nullptr;            // device basis, n x (m + 2 b)
+    std::vector<double> B;          // projected matrix, (m + 2 b) x (m + b) column-major
+    int j = 0, mm = 0, k = 0, conv = 0, restarts = 0, matvec = 0;
+    bool done = false, breakdown = false;
+    std::vector<double> T, Z, res;
     std::vector<dense::cd> ev;
     std::vector<int> order;
-    std::vector<double> res;
-    int j = 0, mm = 0, k = 0, conv = 0, restarts = 0, matvec = 0;
-    while (true) {
-        for (int i = 0; i < b; ++i) {
-            in[i] = V + (size_t)(j + i) * n;
-            outp[i] = V + (size_t)(j + b + i) * n;
-        }
-        NS_TRY(st->step_linear_ptrs(in.data(), outp.data(), nsteps));
-        matvec += b;
-        bool breakdown = false;
-        for (int i = 0; i < b; ++i) {
-            const int c = j + b + i, col = j + i;
-            double beta = 0.0;
-            NS_TRY(cgs2(V, n, n, c, V + (size_t)c * n, h.data(), &beta, gs, stream));
-            double hn = 0.0;
-            for (int r = 0; r < c; ++r) {
-                B[r + (size_t)col * ldb] = h[r];
-                hn += h[r] * h[r];
-            }
-            B[c + (size_t)col * ldb] = beta;
-            if (!std::isfinite(beta)) {
-                set_error("block_arnoldi_eigs: non-finite values in the Krylov basis");
-                return NSSTAB_DIVERGED;
-            }
-            if (beta <= 1e-14 * std::max(1.0, std::sqrt(hn))) {
-                breakdown = true;   // invariant subspace: the factorisation is exact
-                B[c + (size_t)col * ldb] = 0.0;
-            } else {
-                NS_TRY(vec_scale(V + (size_t)c * n, V + (size_t)c * n, n, 1.0 / beta, stream));
-            }
-        }
-        j += b;
-        if (j < m && !breakdown) continue;
-        // full factorisation of order mm: Schur form, Ritz values, residuals ||R y||
-        mm = j;
-        T.assign((size_t)mm * mm, 0.0);
-        Z.assign((size_t)mm * mm, 0.0);
-        for (int c = 0; c < mm; ++c) {
-            Z[c + (size_t)c * mm] = 1.0;
-            for (int r = 0; r < mm; ++r) T[r + (size_t)c * mm] = B[r + (size_t)c * ldb];
-        }
-        dense::hessenberg(mm, T.data(), Z.data());
-        if (dense::schur(mm, T.data(), Z.data()) != 0) {
-            set_error("block_arnoldi_eigs: QR iteration on the projected matrix did not converge");
-            return NSSTAB_ERR_NUMERICAL;
-        }
-        ev = dense::schur_eigenvalues(mm, T.data());
-        order = leading_order(ev);
-        k = take_leading(ev, order, nev);
-        res.assign(k, 0.0);
-        conv = 0;
-        for (int s2 = 0; s2 < k; ++s2) {
-            const std::vector<dense::cd> y = ritz_vector(mm, T.data(), Z.data(), ev, order[s2]);
-            double r2 = 0.0;
-            for (int q = 0; q < b; ++q) {
-                dense::cd acc = 0.0;
-                for (int c = 0; c < mm; ++c) acc += B[(mm + q) + (size_t)c * ldb] * y[c];
-                r2 += std::norm(acc);
-            }
-            res[s2] = std::sqrt(r2);
-            if (res[s2] <= tol) ++conv;
-        }
-        if (conv >= k || restarts >= max_restarts || breakdown) break;
-        // restart: keep p Schur vectors and the b residual columns.  A block
-        // basis of mm columns holds only mm / b powers of M, so keeping just
-        // the values with |mu| >= 1 - delta (the single-vector rule) can
-        // leave too small a space to converge a clustered spectrum (seen to
-        // stall); keep at least half of the basis beyond the k wanted.
-        int p = 0;
-        for (const auto& e : ev)
-            if (std::abs(e) >= 1.0 - delta) ++p;
-        p = std::max(k, std::min(std::max(p, k + (mm - k) / 2), mm - b));
-        std::vector<double> mags(mm);
-        for (int s2 = 0; s2 < mm; ++s2) mags[s2] = std::abs(ev[s2]);
-        std::sort(mags.begin(), mags.end(), std::greater<double>());
-        const double thr = mags[p - 1] * (1.0 - 1e-12);
-        const int psel =
-            dense::schur_reorder(mm, T.data(), Z.data(), [&](dense::cd e) { return std::abs(e) >= thr; });
-        if (psel <= 0 || psel + b > mm) {
-            set_error("block_arnoldi_eigs: Schur reordering failed");
-            return NSSTAB_ERR_NUMERICAL;
-        }
-        p = psel;
-        NS_CUDA(cudaMemcpyAsync(Cd.p, Z.data(), (size_t)mm * p * sizeof(double), cudaMemcpyHostToDevice, stream));
-        NS_TRY(basis_combine(V, n, n, mm, Cd.p, p, tmp.p, n, stream));
-        NS_CUDA(cudaMemcpyAsync(V, tmp.p, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, stream));
-        NS_CUDA(cudaMemcpyAsync(V + (size_t)p * n, V + (size_t)mm * n, (size_t)n * b * sizeof(double),
-                                cudaMemcpyDeviceToDevice, stream));
-        std::vector<double> Bn((size_t)ldb * (m + b), 0.0);
-        for (int c = 0; c < p; ++c) {
-            for (int r = 0; r < p; ++r) Bn[r + (size_t)c * ldb] = T[r + (size_t)c * mm];
-            for (int q = 0; q < b; ++q) {
-                double acc = 0.0;
-                for (int r = 0; r < mm; ++r) acc += B[(mm + q) + (size_t)r * ldb] * Z[r + (size_t)c * mm];
-                Bn[(p + q) + (size_t)c * ldb] = acc;
-            }
-        }
-        B.swap(Bn);
-        NS_CUDA(cudaStreamSynchronize(stream));   // Z upload done before Cd is reused
-        j = p;
-        ++restarts;
+};
+}  // namespace
+
+int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
+                      double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs) {
+    const double delta = 0.05;
+    const int S = st->sets();
+    const int b = st->members() / S;
+    const int ncol = m + 2 * b;      // basis columns held
+    const int ldb = m + 2 * b;       // rows of the projected matrix
+    outs.resize(S);
+    DevBuf Vd, tmp, Cd;
+    NS_CUDA(cudaMalloc(&Vd.p, (size_t)S * n * ncol * sizeof(double)));
+    NS_CUDA(cudaMalloc(&Cd.p, (size_t)ncol * ncol * sizeof(double)));
+    NS_CUDA(cudaMalloc(&tmp.p, (size_t)n * ncol * sizeof(double)));
+    GsBatch gs;
+    struct Release {
+        GsBatch& g;
+        ~Release() { g.release(); }
+    } rel{gs};
+    NS_TRY(gs.alloc(S, ncol));
+    std::vector<BlockProb> pr(S);
+    std::vector<const double*> Vp(S);
+    std::vector<double*> wv(S), sp(S);
+    std::vector<int> jv(S);
+    std::vector<double> H((size_t)S * ncol), beta(S), nrm(S), inv(S);
+    for (int s = 0; s < S; ++s) {
+        pr[s].V = Vd.p + (size_t)s * n * ncol;
+        pr[s].B.assign((size_t)ldb * (m + b), 0.0);
+        Vp[s] = pr[s].V;
     }
-    out.n_eig = k;
-    out.n_conv = conv;
-    out.n_matvec = matvec;
-    out.restarts = restarts;
-    out.mu.resize(k);
-    out.resid = res;
-    for (int s2 = 0; s2 < k; ++s2) out.mu[s2] = ev[order[s2]];
-    out.status = (conv >= k) ? NSSTAB_OK : NSSTAB_NOT_CONVERGED;
-    out.done_at = steady_seconds();
-    if (out.eigvecs) {
-        std::vector<double> Y((size_t)mm * k, 0.0);
-        int s2 = 0;
-        while (s2 < k) {
-            const std::vector<dense::cd> y = ritz_vector(mm, T.data(), Z.data(), ev, order[s2]);
-            if (ev[order[s2]].imag() != 0.0 && s2 + 1 < k) {
-                for (int r = 0; r < mm; ++r) {
-                    Y[r + (size_t)s2 * mm] = y[r].real();
-                    Y[r + (size_t)(s2 + 1) * mm] = y[r].imag();
-                }
-                s2 += 2;
-            } else {
-                for (int r = 0; r < mm; ++r) Y[r + (size_t)s2 * mm] = y[r].real();
-                s2 += 1;
+    // orthonormal start blocks: column i of every set in one batched CGS2
+    for (int i = 0; i < b; ++i) {
+        for (int s = 0; s < S; ++s) {
+            wv[s] = pr[s].V + (size_t)i * n;
+            NS_CUDA(cudaMemcpyAsync(wv[s], v0[(size_t)s * b + i], n * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    stream));
+            jv[s] = 0;
+        }
+        NS_TRY(cgs2_batch(S, Vp.data(), n, n, jv.data(), wv.data(), H.data(), ncol, nrm.data(), gs, stream));
+        std::fill(jv.begin(), jv.end(), i);
+        NS_TRY(cgs2_batch(S, Vp.data(), n, n, jv.data(), wv.data(), H.data(), ncol, beta.data(), gs, stream));
+        for (int s = 0; s < S; ++s) {
+            if (!(nrm[s] > 0.0) || !std::isfinite(nrm[s]) || !(beta[s] > 1e-10 * nrm[s])) {
+                set_error("block_arnoldi_eigs: start vectors are zero, non-finite or linearly dependent");
+                return NSSTAB_ERR_INVALID_ARG;
+            }
+            inv[s] = 1.0 / beta[s];
+        }
+        NS_TRY(scale_batch(S, wv.data(), n, inv.data(), gs, stream));
+    }
+    std::vector<const double*> in((size_t)S * b);
+    std::vector<double*> outp((size_t)S * b);
+    while (true) {
+        int active = 0;
+        for (int s = 0; s < S; ++s) {
+            BlockProb& P = pr[s];
+            for (int i = 0; i < b; ++i) {
+                in[(size_t)s * b + i] = P.done ? nullptr : P.V + (size_t)(P.j + i) * n;
+                outp[(size_t)s * b + i] = P.done ? nullptr : P.V + (size_t)(P.j + b + i) * n;
+            }
+            if (!P.done) {
+                ++active;
+                P.matvec += b;
+                P.breakdown = false;
             }
         }
-        NS_CUDA(cudaMemcpyAsync(Cd.p, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
-        NS_TRY(basis_combine(V, n, n, mm, Cd.p, k, out.eigvecs, n, stream));
+        if (active == 0) break;
+        NS_TRY(st->step_linear_ptrs(in.data(), outp.data(), nsteps));
+        for (int i = 0; i < b; ++i) {
+            for (int s = 0; s < S; ++s) {
+                const BlockProb& P = pr[s];
+                jv[s] = P.done ? -1 : P.j + b + i;
+                wv[s] = P.done ? nullptr : P.V + (size_t)(P.j + b + i) * n;
+            }
+            NS_TRY(cgs2_batch(S, Vp.data(), n, n, jv.data(), wv.data(), H.data(), ncol, beta.data(), gs, stream));
+            for (int s = 0; s < S; ++s) {
+                BlockProb& P = pr[s];
+                sp[s] = nullptr;
+                inv[s] = 0.0;
+                if (P.done) continue;
+                const int c = P.j + b + i, col = P.j + i;
+                double hn = 0.0;
+                for (int r = 0; r < c; ++r) {
+                    P.B[r + (size_t)col * ldb] = H[(size_t)s * ncol + r];
+                    hn += H[(size_t)s * ncol + r] * H[(size_t)s * ncol + r];
+                }
+                P.B[c + (size_t)col * ldb] = beta[s];
+                if (!std::isfinite(beta[s])) {
+                    set_error("block_arnoldi_eigs: non-finite values in the Krylov basis");
+                    return NSSTAB_DIVERGED;
+                }
+                if (beta[s] <= 1e-14 * std::max(1.0, std::sqrt(hn))) {
+                    P.breakdown = true;   // invariant subspace: the factorisation is exact
+                    P.B[c + (size_t)col * ldb] = 0.0;
+                } else {
+                    sp[s] = wv[s];
+                    inv[s] = 1.0 / beta[s];
+                }
+            }
+            NS_TRY(scale_batch(S, sp.data(), n, inv.data(), gs, stream));
+        }
+        for (int s = 0; s < S; ++s) {
+            BlockProb& P = pr[s];
+            if (P.done) continue;
+            P.j += b;
+            if (P.j < m && !P.breakdown) continue;
+            // full factorisation of order mm: Schur form, Ritz values, residuals ||R y||
+            const int mm = P.j;
+            P.mm = mm;
+            P.T.assign((size_t)mm * mm, 0.0);
+            P.Z.assign((size_t)mm * mm, 0.0);
+            for (int c = 0; c < mm; ++c) {
+                P.Z[c + (size_t)c * mm] = 1.0;
+                for (int r = 0; r < mm; ++r) P.T[r + (size_t)c * mm] = P.B[r + (size_t)c * ldb];
+            }
+            dense::hessenberg(mm, P.T.data(), P.Z.data());
+            if (dense::schur(mm, P.T.data(), P.Z.data()) != 0) {
+                set_error("block_arnoldi_eigs: QR iteration on the projected matrix did not converge");
+                return NSSTAB_ERR_NUMERICAL;
+            }
+            P.ev = dense::schur_eigenvalues(mm, P.T.data());
+            P.order = leading_order(P.ev);
+            P.k = take_leading(P.ev, P.order, nev);
+            P.res.assign(P.k, 0.0);
+            P.conv = 0;
+            for (int s2 = 0; s2 < P.k; ++s2) {
+                const std::vector<dense::cd> y = ritz_vector(mm, P.T.data(), P.Z.data(), P.ev, P.order[s2]);
+                double r2 = 0.0;
+                for (int q = 0; q < b; ++q) {
+                    dense::cd acc = 0.0;
+                    for (int c = 0; c < mm; ++c) acc += P.B[(mm + q) + (size_t)c * ldb] * y[c];
+                    r2 += std::norm(acc);
+                }
+                P.res[s2] = std::sqrt(r2);
+                if (P.res[s2] <= tol) ++P.conv;
+            }
+            if (P.conv >= P.k || P.restarts >= max_restarts || P.breakdown) {
+                P.done = true;
+                outs[s].done_at = steady_seconds();
+                continue;
+            }
+            // restart: keep p Schur vectors and the b residual columns.  A
+            // block basis of mm columns holds only mm / b powers of M, so
+            // keeping just the values with |mu| >= 1 - delta (the
+            // single-vector rule) can leave too small a space to converge a
+            // clustered spectrum (seen to stall); keep at least half of the
+            // basis beyond the k wanted.
+            int p = 0;
+            for (const auto& e : P.ev)
+                if (std::abs(e) >= 1.0 - delta) ++p;
+            p = std::max(P.k, std::min(std::max(p, P.k + (mm - P.k) / 2), mm - b));
+            std::vector<double> mags(mm);
+            for (int s2 = 0; s2 < mm; ++s2) mags[s2] = std::abs(P.ev[s2]);
+            std::sort(mags.begin(), mags.end(), std::greater<double>());
+            const double thr = mags[p - 1] * (1.0 - 1e-12);
+            const int psel =
+                dense::schur_reorder(mm, P.T.data(), P.Z.data(), [&](dense::cd e) { return std::abs(e) >= thr; });
+            if (psel <= 0 || psel + b > mm) {
+                set_error("block_arnoldi_eigs: Schur reordering failed");
+                return NSSTAB_ERR_NUMERICAL;
+            }
+            p = psel;
+            NS_CUDA(cudaMemcpyAsync(Cd.p, P.Z.data(), (size_t)mm * p * sizeof(double), cudaMemcpyHostToDevice,
+                                    stream));
+            NS_TRY(basis_combine(P.V, n, n, mm, Cd.p, p, tmp.p, n, stream));
+            NS_CUDA(cudaMemcpyAsync(P.V, tmp.p, (size_t)n * p * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+            NS_CUDA(cudaMemcpyAsync(P.V + (size_t)p * n, P.V + (size_t)mm * n, (size_t)n * b * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, stream));
+            std::vector<double> Bn((size_t)ldb * (m + b), 0.0);
+            for (int c = 0; c < p; ++c) {
+                for (int r = 0; r < p; ++r) Bn[r + (size_t)c * ldb] = P.T[r + (size_t)c * mm];
+                for (int q = 0; q < b; ++q) {
+                    double acc = 0.0;
+                    for (int r = 0; r < mm; ++r) acc += P.B[(mm + q) + (size_t)r * ldb] * P.Z[r + (size_t)c * mm];
+                    Bn[(p + q) + (size_t)c * ldb] = acc;
+                }
+            }
+            P.B.swap(Bn);
+            NS_CUDA(cudaStreamSynchronize(stream));   // Z upload done before Cd is reused
+            P.j = p;
+            ++P.restarts;
+        }
+    }
+    for (int s = 0; s < S; ++s) {
+        BlockProb& P = pr[s];
+        ArnoldiOut& out = outs[s];
+        out.n_eig = P.k;
+        out.n_conv = P.conv;
+        out.n_matvec = P.matvec;
+        out.restarts = P.restarts;
+        out.mu.resize(P.k);
+        out.resid = P.res;
+        for (int s2 = 0; s2 < P.k; ++s2) out.mu[s2] = P.ev[P.order[s2]];
+        out.status = (P.conv >= P.k) ? NSSTAB_OK : NSSTAB_NOT_CONVERGED;
+        if (out.eigvecs) {
+            const int mm = P.mm;
+            std::vector<double> Y((size_t)mm * P.k, 0.0);
+            int s2 = 0;
+            while (s2 < P.k) {
+                const std::vector<dense::cd> y = ritz_vector(mm, P.T.data(), P.Z.data(), P.ev, P.order[s2]);
+                if (P.ev[P.order[s2]].imag() != 0.0 && s2 + 1 < P.k) {
+                    for (int r = 0; r < mm; ++r) {
+                        Y[r + (size_t)s2 * mm] = y[r].real();
+                        Y[r + (size_t)(s2 + 1) * mm] = y[r].imag();
+                    }
+                    s2 += 2;
+                } else {
+                    for (int r = 0; r < mm; ++r) Y[r + (size_t)s2 * mm] = y[r].real();
+                    s2 += 1;
+                }
+            }
+            NS_CUDA(cudaMemcpyAsync(Cd.p, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
+            NS_TRY(basis_combine(P.V, n, n, mm, Cd.p, P.k, out.eigvecs, n, stream));
+            NS_CUDA(cudaStreamSynchronize(stream));
+        }
     }
     NS_CUDA(cudaStreamSynchronize(stream));
     return NSSTAB_OK;

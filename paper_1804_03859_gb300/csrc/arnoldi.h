@@ -27,11 +27,13 @@ double steady_seconds();
 int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
                       double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs);
 
-// One eigenproblem solved with a block of b = st->members() vectors per
-// product with M (block Krylov-Schur); the members must share one base flow
-// (one parameter set).  v0: host array of b device pointers (the start
-// block, linearly independent).  Requires m >= 2 (nev + 1) + 2 b.
+// Block Krylov-Schur: one eigenproblem per parameter set of the stepper,
+// each with a block of b = members / sets vectors per product with M (the b
+// members of a set share its base flow), all sets in lockstep rounds.
+// v0: host array of `members` device pointers (set s's start block is
+// v0[s b .. s b + b - 1], linearly independent); outs[s] receives set s's
+// results.  Requires m >= 2 (nev + 1) + 2 b.
 int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
-                      double tol, int max_restarts, int nsteps, ArnoldiOut& out);
+                      double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs);
 
 }  // namespace nsstab

@@ -257,8 +257,8 @@ int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const doubl
                        int* n_eig, int* n_conv, int* n_matvec) {
     if (!st || !v0 || !eig_re || !eig_im || !resid || !n_eig || !n_conv || !n_matvec)
         return bad_arg("block_arnoldi_eigs: null argument");
-    if (st->impl->sets() != 1) return bad_arg("block_arnoldi_eigs: the stepper must have one parameter set");
-    const int b = st->impl->members();
+    const int S = st->impl->sets();
+    const int b = st->impl->members() / S;
     const long n = (long)st->cfg.nx * st->cfg.ny;
     if (nev < 1) return bad_arg("block_arnoldi_eigs: need nev >= 1");
     if (m > 1024 || m + 2L * b >= n || m < 2 * (nev + 1) + 2 * b)
@@ -273,21 +273,27 @@ int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const doubl
     } else if (!st->have_base) {
         return bad_arg("block_arnoldi_eigs: no base flow (pass base_omega or call stepper_set_base)");
     }
-    std::vector<const double*> v0p(b);
-    for (int i = 0; i < b; ++i) v0p[i] = v0 + (size_t)i * n;
-    ArnoldiOut out;
-    out.eigvecs = eigvecs;
-    const int rc = block_arnoldi_run(st->impl, st->stream, n, v0p.data(), m, nev, tol, max_restarts, nsteps, out);
+    std::vector<const double*> v0p((size_t)S * b);
+    for (size_t i = 0; i < v0p.size(); ++i) v0p[i] = v0 + i * n;
+    std::vector<ArnoldiOut> outs(S);
+    if (eigvecs)
+        for (int s = 0; s < S; ++s) outs[s].eigvecs = eigvecs + (size_t)s * (nev + 1) * n;
+    const int rc = block_arnoldi_run(st->impl, st->stream, n, v0p.data(), m, nev, tol, max_restarts, nsteps, outs);
     if (rc < 0) return rc;
-    for (int s = 0; s < out.n_eig; ++s) {
-        eig_re[s] = out.mu[s].real();
-        eig_im[s] = out.mu[s].imag();
-        resid[s] = out.resid[s];
+    int status = rc;
+    for (int s = 0; s < S; ++s) {
+        const ArnoldiOut& o = outs[s];
+        for (int q = 0; q < o.n_eig; ++q) {
+            eig_re[(size_t)s * (nev + 1) + q] = o.mu[q].real();
+            eig_im[(size_t)s * (nev + 1) + q] = o.mu[q].imag();
+            resid[(size_t)s * (nev + 1) + q] = o.resid[q];
+        }
+        n_eig[s] = o.n_eig;
+        n_conv[s] = o.n_conv;
+        n_matvec[s] = o.n_matvec;
+        if (status == NSSTAB_OK && o.status != NSSTAB_OK) status = o.status;
     }
-    *n_eig = out.n_eig;
-    *n_conv = out.n_conv;
-    *n_matvec = out.n_matvec;
-    return rc != NSSTAB_OK ? rc : out.status;
+    return status;
 }
 
 int apply_tangent(nsstab_stepper* st, const double* q, const double* v_in, double* v_out, double T) {

@@ -538,25 +538,34 @@ class Stepper:
         return EigResult(re[:k] + 1j * im[:k], res[:k], n_conv.value, n_mv.value, rc)
 
     def block_arnoldi_eigs(self, base, v0, m: int, nev: int, tol: float, T: float, max_restarts: int = 0,
-                           eigvecs=None) -> EigResult:
-        """One eigenproblem with a block of ``members`` vectors per product
-        with M (a stepper made as ``Stepper(per_set=b, Re=scalar, ...)``);
-        v0: [b, ny, nx] start block."""
-        re, im, res = np.zeros(nev + 1), np.zeros(nev + 1), np.zeros(nev + 1)
-        n_eig, n_conv, n_mv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        bp = self._p(base, "base", 1) if base is not None else None
+                           eigvecs=None):
+        """Block Krylov-Schur with b = ``per_set`` vectors per product with M,
+        one eigenproblem per parameter set (a stepper made as
+        ``Stepper(per_set=b, Re=..., ...)``); v0: [sets * b, ny, nx], set s's
+        start block in rows s*b .. s*b + b - 1.  Returns an EigResult for a
+        single parameter set, else a list of them (one per set)."""
+        S = self.sets
+        re, im, res = (np.zeros((S, nev + 1)) for _ in range(3))
+        n_eig, n_conv, n_mv = (np.zeros(S, dtype=np.int32) for _ in range(3))
+        bp = self._p(base, "base", S) if base is not None else None
         ev = None
         if eigvecs is not None:
-            if eigvecs.shape[0] < nev + 1:
-                raise ValueError("eigvecs must hold nev + 1 fields")
+            if eigvecs.numel() < S * (nev + 1) * self.shape[0] * self.shape[1]:
+                raise ValueError("eigvecs must hold sets * (nev + 1) fields")
             ev = _field_ptr(eigvecs, self.shape, "eigvecs")
+        ip = lambda a: a.ctypes.data_as(_ip)
         rc = _check(self._lib.block_arnoldi_eigs(self._h, bp, self._p(v0, "v0"), int(m), int(nev), float(tol),
                                                  int(max_restarts), float(T), re.ctypes.data_as(_dp),
-                                                 im.ctypes.data_as(_dp), res.ctypes.data_as(_dp), ev,
-                                                 ctypes.byref(n_eig), ctypes.byref(n_conv), ctypes.byref(n_mv)),
+                                                 im.ctypes.data_as(_dp), res.ctypes.data_as(_dp), ev, ip(n_eig),
+                                                 ip(n_conv), ip(n_mv)),
                     "block_arnoldi_eigs", allow_soft=True)
-        k = n_eig.value
-        return EigResult(re[:k] + 1j * im[:k], res[:k], n_conv.value, n_mv.value, rc)
+        out = []
+        for s in range(S):
+            k = int(n_eig[s])
+            status = OK if n_conv[s] >= k else NOT_CONVERGED
+            out.append(EigResult(re[s, :k] + 1j * im[s, :k], res[s, :k], int(n_conv[s]), int(n_mv[s]),
+                                 rc if S == 1 else status))
+        return out[0] if S == 1 else out
 
     KERNELS = ("col_poisson", "row_inverse_psi", "row_forward_rhs", "col_update", "row_inverse_star",
                "row_forward_pen")
