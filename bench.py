@@ -470,6 +470,7 @@ def run_native(args, rank: int, world: int):
     serving = None
     if not args.no_serve and not args.no_eigs:
         serving = serve_leg(args, dev)
+    bblock = None if (args.no_batch or world > 1) else batched_block_leg(args, dev)
     unet_leg = None if args.no_serve else unet_train_leg(args, dev)
     newton_leg = None if (args.no_serve or args.no_eigs) else newton_leg_run(args, dev)
     wake_leg = None if (args.no_serve or args.no_eigs) else wake_stability_leg(args, dev)
@@ -508,12 +509,113 @@ def run_native(args, rank: int, world: int):
         "step_tflops_fp64": step_flops * nsteps / (el64 / args.steps) / 1e12,
         "time_to_eigs": eigs,
         "batched": batched,
+        "batched_block": bblock,
         "serving": serving,
         "unet": unet_leg,
         "newton": newton_leg,
         "wake_stability": wake_leg,
     }
     print(json.dumps(out))
+
+
+BB_SETS = 16
+
+
+def batched_block_leg(args, dev, rate_grid=(2048, 1024), rate_block=8, rate_steps=40, eig_grid=(256, 128),
+                      eig_block=2, eig_m=128, single_m=128, restarts=30):
+    """Block Krylov-Schur over a Reynolds sweep: 16 Reynolds numbers in
+    40..100, each its own eigenproblem with a block of b vectors per product
+    with M, FP32 stepper, all 16 b fields advanced by one launch per kernel.
+    (1) Throughput of one lockstep round's product at 2048x1024 with b = 8
+    (128 fields, ~268 M points per launch, far beyond L2): `rate_steps`
+    linearised steps timed with CUDA events.  (2) Time to the leading 4
+    eigenvalues of all 16 sets at 256x128 (tol 1e-6) with b = 2, m = 128,
+    against the same 16 solves by the batched single-vector driver and
+    against plain FP64 single solves run one after another (one measured,
+    times 16)."""
+    import torch
+
+    from paper_1804_03859_gb300 import inputs, nsstab
+
+    Res = [float(x) for x in np.linspace(40.0, 100.0, BB_SETS)]
+    out = {"sets": BB_SETS, "Re": [Res[0], Res[-1]], "precision": "f32"}
+    if rate_grid is not None:
+        nx, ny = rate_grid
+        dt = 0.01 * 128 / nx
+        block = rate_block
+        st = nsstab.Stepper(nx=nx, ny=ny, dt=dt, Re=Res, per_set=block, precision=32)
+        if not args.no_tune:
+            st.stepper_autotune(reps=2)
+        base = torch.from_numpy(inputs.wake_like_field(ny, nx, seed=0)).to(dev)
+        st.stepper_set_base(base.expand(BB_SETS, ny, nx).contiguous())
+        del base
+        g = torch.from_numpy(np.stack([inputs.gaussian_field(ny, nx, seed=500 + i) for i in range(block)])).to(dev)
+        v = g.repeat(BB_SETS, 1, 1)
+        del g
+        w = torch.empty_like(v)
+        T = rate_steps * dt
+        st.apply_expTL(None, v, w, T)
+        reps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            st.apply_expTL(None, v, w, T)
+        e1.record()
+        e1.synchronize()
+        sec = e0.elapsed_time(e1) / 1e3 / reps
+        fields = BB_SETS * block
+        out["rate"] = {"grid": [nx, ny], "block": block, "fields_per_launch": fields, "steps_timed": rate_steps,
+                       "reps": reps, "value": fields * nx * ny * rate_steps / sec, "unit": UNIT,
+                       "ms_per_step_all_fields": 1e3 * sec / rate_steps,
+                       "seconds_per_round_at_T_0_5": sec * round(0.5 / dt) / rate_steps,
+                       "l2": "inputs far larger than L2 (128 fields x 2M points)", "plans": st.plans()}
+        del st, v, w
+        torch.cuda.empty_cache()
+    if eig_grid is not None and not args.no_eigs:
+        nx, ny = eig_grid
+        dt = 0.01 * 128 / nx
+        kw = dict(nx=nx, ny=ny, dt=dt)
+        block = eig_block
+        bases = torch.from_numpy(np.stack([inputs.wake_like_field(ny, nx, seed=k) for k in range(BB_SETS)])).to(dev)
+        v = torch.from_numpy(np.stack([inputs.gaussian_field(ny, nx, seed=600 + i)
+                                       for i in range(BB_SETS * block)])).to(dev)
+        runs = {}
+        stb = nsstab.Stepper(Re=Res, per_set=block, precision=32, **kw)
+        if not args.no_tune:
+            stb.stepper_autotune(reps=3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = stb.block_arnoldi_eigs(bases, v, m=eig_m, nev=4, tol=TOL32, T=T_SAMPLE, max_restarts=restarts)
+        runs["block"] = {"seconds": time.perf_counter() - t0, "b": block, "m": eig_m,
+                         "sets_converged": int(sum(r.n_conv >= len(r.mu) for r in rs)),
+                         "products_total": int(sum(r.n_matvec for r in rs))}
+        ref = rs
+        del stb
+        sts = nsstab.Stepper(Re=Res, precision=32, **kw)
+        if not args.no_tune:
+            sts.stepper_autotune(reps=3)
+        v1 = v[::block].contiguous()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rs = sts.batch_arnoldi_eigs(bases, v1, m=single_m, nev=4, tol=TOL32, T=T_SAMPLE, max_restarts=restarts)
+        runs["single_vector_batched"] = {"seconds": time.perf_counter() - t0, "m": single_m,
+                                         "sets_converged": int(sum(r.n_conv >= len(r.mu) for r in rs)),
+                                         "products_total": int(sum(r.n_matvec for r in rs))}
+        agree = [float(max(np.min(np.abs(b.mu - x)) / abs(x) for x in a.mu)) for a, b in zip(ref, rs)
+                 if a.n_conv >= len(a.mu) and b.n_conv >= len(b.mu)]
+        del sts
+        st64 = nsstab.Stepper(Re=Res[0], **kw)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64 = st64.arnoldi_eigs(bases[0], v1[0], m=single_m, nev=4, tol=1e-8, T=T_SAMPLE, max_restarts=restarts)
+        one = time.perf_counter() - t0
+        runs["plain_fp64_sequential_estimate"] = {"seconds": 16 * one, "one_solve_seconds": one, "m": single_m,
+                                                  "tol": 1e-8, "converged": bool(r64.n_conv >= len(r64.mu))}
+        out["time_to_eigs"] = {"grid": [nx, ny], "nev": 4, "tol": TOL32, "T": T_SAMPLE, **runs,
+                               "max_rel_diff_block_vs_single": max(agree) if agree else None}
+    return out
 
 
 def newton_leg_run(args, dev):
