@@ -71,6 +71,8 @@ def parse():
                     help="only run --steps linearised steps of one stepper on this grid (for ncu captures)")
     ap.add_argument("--precision", type=int, default=64, help="stepper precision of --profile-case (64, 48, 32)")
     ap.add_argument("--members", type=int, default=1, help="batch members of --profile-case")
+    ap.add_argument("--profile-unet", action="store_true",
+                    help="only run the U-Net training leg (3 + 20 steps; for ncu launch lists)")
     return ap.parse_args()
 
 
@@ -782,6 +784,14 @@ def main():
     args = parse()
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.profile_unet:
+        import torch
+
+        from paper_1804_03859_gb300 import build
+
+        build.build()
+        print(json.dumps(unet_train_leg(args, torch.device("cuda"))))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
