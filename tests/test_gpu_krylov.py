@@ -272,3 +272,19 @@ def test_double_float_arnoldi_matches_dense(small):
     res = st.arnoldi_eigs(_dev(base), _dev(v0), m=150, nev=4, tol=1e-10, T=T)
     assert res.status == nsstab.OK and res.n_conv == len(res.mu)
     assert _match(res.mu, mu_dense[:6]) <= 1e-10
+
+
+def test_batched_block_fp32_tracks_fp64():
+    """The batched block solve with the FP32 stepper: every set's leading
+    eigenvalues within 1e-5 relative of the FP64 stepper's (same sets, same
+    start blocks)."""
+    kw = dict(nx=64, ny=32, dt=0.02, Re=[45.0, 65.0], per_set=2)
+    bases = _dev(np.stack([inputs.wake_like_field(32, 64, seed=90 + s) for s in range(2)]))
+    v0 = _dev(np.stack([inputs.gaussian_field(32, 64, seed=95 + i) for i in range(4)]))
+    ref = nsstab.Stepper(**kw).block_arnoldi_eigs(bases, v0, m=48, nev=4, tol=1e-9, T=0.4, max_restarts=100)
+    got = nsstab.Stepper(precision=32, **kw).block_arnoldi_eigs(bases, v0, m=48, nev=4, tol=1e-6, T=0.4,
+                                                                max_restarts=100)
+    for r, g in zip(ref, got):
+        assert r.n_conv == len(r.mu) and g.n_conv == len(g.mu)
+        for mu in g.mu:
+            assert np.min(np.abs(r.mu - mu)) <= 1e-5 * abs(mu)

@@ -42,7 +42,11 @@ def _rel(a, b):
 # move under a 1e-7 perturbation of its input).  At width 16 such a perturbation already moves the
 # oracle's own output by 5.5e-3 (flipped roundings propagate through 14 layers), so that case is held
 # to the size of the bfloat16 effect itself (1.2e-2 between bfloat16 and exact storage) instead.
+# Widths and input channels also select the GEMMs' copy paths: 16-byte copies need channel counts that are
+# multiples of 8 (width 4: none; width 12: some layers; widths 8, 16: all; in_ch 8: the first layer's
+# input unpadded).
 CASES = [(2, 4, 16, 32, 2, 3e-3, 1e-2, 5e-2), (2, 8, 32, 64, 3, 3e-3, 1e-2, 5e-2),
+         (8, 8, 16, 32, 2, 3e-3, 1e-2, 5e-2), (2, 12, 16, 32, 2, 3e-3, 1e-2, 5e-2),
          (3, 16, 64, 128, 2, 2.5e-2, 5e-2, 0.2)]
 
 
