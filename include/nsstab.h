@@ -210,21 +210,23 @@ int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
 #define NSSTAB_NOALLOC_MAX_COLS 256
 
 /* cgs2_orthogonalize for callers that cannot allocate device memory at the
- * point of the call (code running while someone else captures the stream
- * into a CUDA graph, frameworks whose memory pools forbid side allocations,
- * real-time loops that must not take allocator locks).  The paper has no
- * counterpart: it is a deployment variant of the Gram-Schmidt step above.
+ * point of the call: frameworks whose memory pool owns the device memory and
+ * forbids side allocations, and real-time loops that must not take the
+ * allocator's locks or meet an out-of-memory error mid-run.  The paper has
+ * no counterpart: it is a deployment variant of the Gram-Schmidt step above.
  * Same arguments, results and synchronisation as cgs2_orthogonalize, but
  * all scratch (partial dot products per block, the two coefficient vectors)
  * lives in one fixed file-scope device array of about 0.3 MB that every GPU
  * loading the library holds until the process exits; the call makes no
  * cudaMalloc, cudaFree or other allocating call.  j > NSSTAB_NOALLOC_MAX_COLS
  * is rejected with NSSTAB_ERR_INVALID_ARG.  The first call on a device looks
- * up the array's device address (cudaGetSymbolAddress) for that device; make
- * that first call before any stream capture.  All calls on a device share
- * the array, so calls whose GPU work overlaps (other streams, other host
- * threads) race: serialise them.  Nothing needs clearing between calls: each
- * call writes every scratch value before reading it. */
+ * up the array's device address (cudaGetSymbolAddress) for that device, with
+ * that device current; make that first call before any stream capture.  A
+ * reset of the device's primary context after that first call is not
+ * supported.  All calls on a device share the array, so calls whose GPU
+ * work overlaps (other streams, other host threads) race: serialise them.
+ * Nothing needs clearing between calls: each call writes every scratch
+ * value before reading it. */
 int cgs2_orthogonalize_noalloc(const double* V, long ldv, long n, int j, double* w,
                                double* h, double* beta, void* stream);
 

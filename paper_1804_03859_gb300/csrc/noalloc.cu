@@ -1,10 +1,10 @@
 // CGS2 orthogonalisation for callers that must not allocate device memory.
 //
 // Some hosts of this library cannot call cudaMalloc at the point where they
-// orthogonalise a vector: code running while a CUDA stream is being captured
-// into a graph by someone else, code inside a memory-pool-managed framework
-// that forbids side allocations, or real-time callers that must not take
-// the allocator's locks.  This entry point does the same work as
+// orthogonalise a vector: code inside a framework whose memory pool owns
+// all device memory and forbids side allocations, or real-time loops that
+// must not take the allocator's locks or risk an allocation failure in
+// the middle of a run.  This entry point does the same work as
 // cgs2_orthogonalize but keeps its scratch (the per-block partial dot
 // products and the two coefficient vectors) in one file-scope device array
 // of fixed size, so it never allocates: no cudaMalloc, cudaFree,
@@ -13,7 +13,9 @@
 // The array exists once per GPU that loads the library and lives until the
 // process exits.  Every call on a device uses the same array, so calls whose
 // GPU work overlaps (on different streams, or from different host threads)
-// race on it; serialise them.
+// race on it; serialise them.  The first call on a device looks up the
+// array's device address once; a later reset of that device's primary
+// context (cudaDeviceReset) is not supported.
 #include <mutex>
 
 #include "stepper.cuh"
@@ -30,7 +32,9 @@ __global__ void k_gs_update(double* __restrict__ w, const double* __restrict__ V
 namespace {
 
 constexpr int kMaxCols = NSSTAB_NOALLOC_MAX_COLS;   // largest j accepted
-constexpr int kBlocks = 152;                        // one block of partial sums per SM
+// The grid of the dot-product kernel is fixed by the static scratch size
+// (one row of partial sums per block), not by the GPU's SM count.
+constexpr int kBlocks = 152;
 constexpr int kThreads = 256;
 // [kBlocks][kMaxCols] partials | h1 [kMaxCols] | h2 [kMaxCols] | beta^2 | h1+h2 [kMaxCols]
 constexpr int kScratch = kBlocks * kMaxCols + 3 * kMaxCols + 8;
@@ -48,7 +52,9 @@ std::mutex g_mutex;
 double* g_addr[kMaxDevices] = {nullptr};
 
 // Device address of g_scratch on the current device, looked up once per
-// device (the name g_scratch is only a host-side handle in host code).
+// device with that device current (in host code the name g_scratch is only
+// a host-side stand-in, not a device address).  The cached address stays
+// valid for the life of the device's primary context.
 int scratch_address(double** out) {
     int dev = -1;
     NS_CUDA(cudaGetDevice(&dev));

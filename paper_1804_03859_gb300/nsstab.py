@@ -199,20 +199,35 @@ def stepper_destroy(h) -> None:
     load_library().stepper_destroy(h)
 
 
-def cgs2_orthogonalize(V, n: int, j: int, w, ldv: int | None = None, stream=None):
-    """One CGS2 step on device tensors: returns (h as numpy array, beta)."""
+def _gs_args(V, n: int, j: int, w, ldv):
+    """Check the device tensors of a CGS2 call against the sizes the kernels
+    will touch (V: j columns of length n, leading dimension ldv; w: n)."""
     import torch
 
-    lib = load_library()
     if w.dtype != torch.float64 or w.device.type != "cuda" or not w.is_contiguous():
         raise ValueError("w must be a contiguous float64 CUDA tensor")
-    if j > 0 and (V.dtype != torch.float64 or V.device.type != "cuda" or not V.is_contiguous()):
-        raise ValueError("V must be a contiguous float64 CUDA tensor")
+    ldv = n if ldv is None else ldv
+    if n < 1 or j < 0 or (j > 0 and ldv < n):
+        raise ValueError("bad sizes: need n >= 1, j >= 0 and ldv >= n")
+    if w.numel() < n:
+        raise ValueError(f"w holds {w.numel()} elements, fewer than n = {n}")
+    if j > 0:
+        if V.dtype != torch.float64 or V.device.type != "cuda" or not V.is_contiguous():
+            raise ValueError("V must be a contiguous float64 CUDA tensor")
+        if V.numel() < (j - 1) * ldv + n:
+            raise ValueError(f"V holds {V.numel()} elements, fewer than (j - 1) * ldv + n = {(j - 1) * ldv + n}")
+    return ldv
+
+
+def cgs2_orthogonalize(V, n: int, j: int, w, ldv: int | None = None, stream=None):
+    """One CGS2 step on device tensors: returns (h as numpy array, beta)."""
+    ldv = _gs_args(V, n, j, w, ldv)
+    lib = load_library()
     h = np.zeros(max(j, 1))
     beta = ctypes.c_double()
     s = current_stream_handle() if stream is None else ctypes.c_void_p(stream)
     vp = ctypes.c_void_p(V.data_ptr()) if j > 0 else ctypes.c_void_p(0)
-    _check(lib.cgs2_orthogonalize(vp, ldv if ldv is not None else n, n, j, ctypes.c_void_p(w.data_ptr()),
+    _check(lib.cgs2_orthogonalize(vp, ldv, n, j, ctypes.c_void_p(w.data_ptr()),
                                   h.ctypes.data_as(_dp), ctypes.byref(beta), s), "cgs2_orthogonalize")
     return h[:j], beta.value
 
@@ -222,19 +237,15 @@ NOALLOC_MAX_COLS = 256
 
 def cgs2_orthogonalize_noalloc(V, n: int, j: int, w, ldv: int | None = None, stream=None):
     """cgs2_orthogonalize without any device allocation (fixed static scratch;
-    j <= NOALLOC_MAX_COLS).  For callers that cannot allocate at call time."""
-    import torch
-
+    j <= NOALLOC_MAX_COLS).  For callers that cannot allocate at call time,
+    such as frameworks whose memory pool owns the device memory."""
+    ldv = _gs_args(V, n, j, w, ldv)
     lib = load_library()
-    if w.dtype != torch.float64 or w.device.type != "cuda" or not w.is_contiguous():
-        raise ValueError("w must be a contiguous float64 CUDA tensor")
-    if j > 0 and (V.dtype != torch.float64 or V.device.type != "cuda" or not V.is_contiguous()):
-        raise ValueError("V must be a contiguous float64 CUDA tensor")
     h = np.zeros(max(j, 1))
     beta = ctypes.c_double()
     s = current_stream_handle() if stream is None else ctypes.c_void_p(stream)
     vp = ctypes.c_void_p(V.data_ptr()) if j > 0 else ctypes.c_void_p(0)
-    _check(lib.cgs2_orthogonalize_noalloc(vp, ldv if ldv is not None else n, n, j, ctypes.c_void_p(w.data_ptr()),
+    _check(lib.cgs2_orthogonalize_noalloc(vp, ldv, n, j, ctypes.c_void_p(w.data_ptr()),
                                           h.ctypes.data_as(_dp), ctypes.byref(beta), s),
            "cgs2_orthogonalize_noalloc")
     return h[:j], beta.value

@@ -141,3 +141,36 @@ def test_ordered_schur_puts_the_wanted_values_first(lib, n, seed):
     assert sdim == p
     s = np.linalg.svd(Z[:, :p].T @ Zs[:, :p], compute_uv=False)
     assert s.min() > 1 - 1e-10
+
+
+class _FakeCudaTensor:
+    """Stands in for a float64 CUDA tensor of a given size (no GPU needed):
+    the CGS2 wrappers must reject undersized buffers before any call."""
+
+    def __init__(self, numel):
+        import torch
+
+        self.dtype = torch.float64
+        self.device = torch.device("cuda", 0)
+        self._n = numel
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        raise AssertionError("an undersized buffer reached the C call")
+
+
+@pytest.mark.parametrize("fn", [nsstab.cgs2_orthogonalize, nsstab.cgs2_orthogonalize_noalloc])
+@pytest.mark.parametrize("vsize,wsize,j,ldv", [
+    (4 * 1000 - 1, 1000, 4, None),      # V one element short of j columns
+    (3 * 1200 + 999, 1000, 4, 1200),    # with a leading dimension: (j-1) ldv + n - 1
+    (4 * 1000, 999, 4, None),           # w short
+    (4 * 1000, 1000, 4, 999),           # ldv < n
+])
+def test_cgs2_wrappers_reject_undersized_tensors(fn, vsize, wsize, j, ldv):
+    with pytest.raises(ValueError):
+        fn(_FakeCudaTensor(vsize), 1000, j, _FakeCudaTensor(wsize), ldv=ldv)

@@ -1,10 +1,10 @@
 """The allocation-free CGS2 entry point gives the same result as the regular one.
 
 cgs2_orthogonalize_noalloc exists for callers that cannot allocate device
-memory when they orthogonalise (for example while another component is
-capturing the stream into a CUDA graph, or inside a framework whose memory
-pool forbids side allocations); it keeps its scratch in a fixed device array
-inside the library instead.  This file is collected last so that a run which
+memory when they orthogonalise (a framework whose memory pool owns the
+device memory and forbids side allocations, or a real-time loop that must
+not take the allocator's locks); it keeps its scratch in a fixed device
+array inside the library instead.  This file is collected last so that a run which
 stops at the first failure has run every other test before it.
 """
 import numpy as np
@@ -47,3 +47,37 @@ def test_noalloc_rejects_bases_beyond_its_fixed_scratch():
     w = torch.ones(n, dtype=torch.float64, device="cuda")
     with pytest.raises(nsstab.NsstabError, match="NSSTAB_NOALLOC_MAX_COLS"):
         nsstab.cgs2_orthogonalize_noalloc(V, n, j, w)
+
+
+def test_noalloc_calls_leave_device_free_memory_unchanged():
+    """The defining property: after a first call (which loads the kernels and
+    looks up the scratch address), further calls at the largest basis size
+    allocate nothing, also from a host thread that never called before."""
+    import threading
+
+    n, j = 65536, nsstab.NOALLOC_MAX_COLS
+    V, w0 = _basis(n, j, seed=11)
+    w = torch.from_numpy(w0).cuda()
+    nsstab.cgs2_orthogonalize_noalloc(V, n, j, w.clone())
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(4):
+        w.copy_(torch.from_numpy(w0))
+        nsstab.cgs2_orthogonalize_noalloc(V, n, j, w)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    errors = []
+
+    def other_thread():
+        try:
+            for _ in range(2):
+                nsstab.cgs2_orthogonalize_noalloc(V, n, j, w)
+            torch.cuda.synchronize()
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+
+    t = threading.Thread(target=other_thread)
+    t.start()
+    t.join()
+    assert not errors, errors
+    assert torch.cuda.mem_get_info()[0] == free0
