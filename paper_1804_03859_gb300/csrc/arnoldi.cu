@@ -303,16 +303,19 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
 
 // Block Krylov-Schur with a block of b vectors per product with M, for
 // every parameter set of the batched stepper at once (b = members / sets;
-// the b members of a set share its base flow).  Column c of a basis is
-// orthogonalised by CGS2 against all columns before it, so
-// M V_j = V_{j+b} B with B banded (b sub-diagonals); the residual of a Ritz
-// pair (theta, V y) is ||R y||, R the b rows of B below the square part.
+// the b members of a set share its base flow).  The b new columns of a
+// round are orthogonalised against the basis by blocked CGS2 (two
+// tall-skinny passes, each reading the basis once for all b columns) and
+// then against each other, which gives column c the same coefficients as
+// Gram-Schmidt against all columns before it, so M V_j = V_{j+b} B with B
+// banded (b sub-diagonals); the residual of a Ritz pair (theta, V y) is
+// ||R y||, R the b rows of B below the square part.
 // The restart keeps the wanted Schur vectors and the b residual columns:
 // M V_p = V_p T_p + V_res (R Z_p), the block form of Sec. 3.2.2's
 // decomposition (Eqs. 60-63 have b = 1).  The sets' processes advance in
 // lockstep rounds: one batched product with M over the b new columns of
-// every unfinished set, then for each of the b columns one batched CGS2
-// across the sets.  A finished set leaves the rounds.
+// every unfinished set, one batched block Gram-Schmidt across the sets,
+// then the b intra-block steps.  A finished set leaves the rounds.
 namespace {
 struct BlockProb {
     double* V = nullptr;            // device basis, n x (m + 2 b)
@@ -342,12 +345,13 @@ int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double
         GsBatch& g;
         ~Release() { g.release(); }
     } rel{gs};
-    NS_TRY(gs.alloc(S, ncol));
+    NS_TRY(gs.alloc(S, ncol * b));   // the block passes' coefficients: (m + b) x b per set
     std::vector<BlockProb> pr(S);
-    std::vector<const double*> Vp(S);
-    std::vector<double*> wv(S), sp(S);
-    std::vector<int> jv(S);
-    std::vector<double> H((size_t)S * ncol), beta(S), nrm(S), inv(S);
+    std::vector<const double*> Vp(S), Vb(S);
+    std::vector<double*> wv(S), sp(S), wb(S);
+    std::vector<int> jv(S), jb(S);
+    const int ldhb = ncol * b;
+    std::vector<double> H((size_t)S * ncol), HB((size_t)S * ldhb), beta(S), nrm(S), inv(S);
     for (int s = 0; s < S; ++s) {
         pr[s].V = Vd.p + (size_t)s * n * ncol;
         pr[s].B.assign((size_t)ldb * (m + b), 0.0);
@@ -391,26 +395,46 @@ int block_arnoldi_run(StepperBase* st, cudaStream_t stream, long n, const double
         }
         if (active == 0) break;
         NS_TRY(st->step_linear_ptrs(in.data(), outp.data(), nsteps));
+        // block Gram-Schmidt: the b new columns of every set against its
+        // J = j + b orthonormal columns in two tall-skinny passes (one read
+        // of the basis per pass for all b columns) ...
+        for (int s = 0; s < S; ++s) {
+            const BlockProb& P = pr[s];
+            jb[s] = P.done ? -1 : P.j + b;
+            wb[s] = P.done ? nullptr : P.V + (size_t)(P.j + b) * n;
+        }
+        NS_TRY(bcgs2_batch(S, Vp.data(), n, n, jb.data(), wb.data(), n, b, HB.data(), ldhb, gs, stream));
+        // ... then CGS2 of each new column against the block's earlier ones:
+        // M v_{j+i} = V_J HB[:, i] + sum_{r < i} q_r h_r + beta q_i, the same
+        // coefficients as column-by-column Gram-Schmidt against all J + i
+        // columns (q_r is orthogonal to V_J)
         for (int i = 0; i < b; ++i) {
             for (int s = 0; s < S; ++s) {
                 const BlockProb& P = pr[s];
-                jv[s] = P.done ? -1 : P.j + b + i;
+                jv[s] = P.done ? -1 : i;
+                Vb[s] = P.V + (size_t)(P.j + b) * n;
                 wv[s] = P.done ? nullptr : P.V + (size_t)(P.j + b + i) * n;
             }
-            NS_TRY(cgs2_batch(S, Vp.data(), n, n, jv.data(), wv.data(), H.data(), ncol, beta.data(), gs, stream));
+            NS_TRY(cgs2_batch(S, Vb.data(), n, n, jv.data(), wv.data(), H.data(), ncol, beta.data(), gs, stream));
             for (int s = 0; s < S; ++s) {
                 BlockProb& P = pr[s];
                 sp[s] = nullptr;
                 inv[s] = 0.0;
                 if (P.done) continue;
-                const int c = P.j + b + i, col = P.j + i;
+                const int J = P.j + b, c = J + i, col = P.j + i;
                 double hn = 0.0;
-                for (int r = 0; r < c; ++r) {
-                    P.B[r + (size_t)col * ldb] = H[(size_t)s * ncol + r];
-                    hn += H[(size_t)s * ncol + r] * H[(size_t)s * ncol + r];
+                for (int r = 0; r < J; ++r) {
+                    const double h = HB[(size_t)s * ldhb + (size_t)r * b + i];
+                    P.B[r + (size_t)col * ldb] = h;
+                    hn += h * h;
+                }
+                for (int r = 0; r < i; ++r) {
+                    const double h = H[(size_t)s * ncol + r];
+                    P.B[J + r + (size_t)col * ldb] = h;
+                    hn += h * h;
                 }
                 P.B[c + (size_t)col * ldb] = beta[s];
-                if (!std::isfinite(beta[s])) {
+                if (!std::isfinite(beta[s]) || !std::isfinite(hn)) {
                     set_error("block_arnoldi_eigs: non-finite values in the Krylov basis");
                     return NSSTAB_DIVERGED;
                 }

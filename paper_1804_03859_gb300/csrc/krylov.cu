@@ -59,6 +59,32 @@ __global__ void k_gs_reduce(const double* __restrict__ partial, int nb, int ldp,
     }
 }
 
+// out[c] = sum_b partial[b * ldp + c] for c < j, over many blocks: each block
+// takes 32 columns, its 8 warps sum interleaved rows of partials, and warp 0
+// adds the 8 warp sums in a fixed order (bit-reproducible run to run).
+// member blockIdx.y: partial + member * nb * ldp, out + member * ldo; js
+// (optional) gives a per-member column count (<= 0: member skipped).
+__global__ void k_gs_reduce_par(const double* __restrict__ partial, int nb, int ldp, int j,
+                                const int* __restrict__ js, double* __restrict__ out, int ldo) {
+    const int b = blockIdx.y;
+    if (js) j = js[b];
+    const int lane = threadIdx.x & 31, wv = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int c = blockIdx.x * 32 + lane;
+    if (j <= 0 || blockIdx.x * 32 >= j) return;
+    partial += (size_t)b * nb * ldp;
+    __shared__ double red[32][33];
+    double s = 0.0;
+    if (c < j)
+        for (int r = wv; r < nb; r += nw) s += partial[(long)r * ldp + c];
+    red[wv][lane] = s;
+    __syncthreads();
+    if (wv == 0 && c < j) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += red[w][lane];
+        out[(size_t)b * ldo + c] = t;
+    }
+}
+
 // w[i] -= sum_c V[c][i] h[c]
 __global__ void k_gs_update(double* __restrict__ w, const double* __restrict__ V, long ldv, long n, int j,
                             const double* __restrict__ h) {
@@ -150,18 +176,6 @@ __global__ void k_gs_dot_b(const double* const* __restrict__ Vs, long ldv, long 
     }
 }
 
-__global__ void k_gs_reduce_b(const double* __restrict__ partial, int nb, int ldp, const int* __restrict__ js,
-                              double* __restrict__ out) {
-    const int b = blockIdx.y;
-    const int j = js[b];
-    const double* part = partial + (size_t)b * nb * ldp;
-    for (int c = threadIdx.x; c < j; c += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < nb; ++k) s += part[(long)k * ldp + c];
-        out[(size_t)b * ldp + c] = s;
-    }
-}
-
 __global__ void k_gs_update_b(double* const* __restrict__ ws, const double* const* __restrict__ Vs, long ldv, long n,
                               const int* __restrict__ js, const double* __restrict__ h, int ldp) {
     const int b = blockIdx.y;
@@ -184,6 +198,162 @@ __global__ void k_scale_b(double* const* __restrict__ ws, long n, const double* 
     if (!w) return;
     const double f = s[blockIdx.y];
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) w[i] *= f;
+}
+
+// ------------------------------------------------ blocked Gram-Schmidt
+// Block form of the Gram-Schmidt step for block Krylov methods: the b new
+// columns W of a set are projected against its first J orthonormal basis
+// columns in one tall-skinny product pair, H = V_J^T W (J x b) and
+// W -= V_J H, so V is read once per pass for all b columns instead of once
+// per column.  Set s = blockIdx.z (dot) / blockIdx.y (update); J[s] <= 0
+// skips the set.  W's columns are ldw apart; H is stored [c * b + q].
+
+static const int kBgsCols = 4;   // basis columns per block row of the dot product
+
+// partial[s][blk][c * B + q] = sum over block blk's row range of V[c][i] W[q][i],
+// for the kBgsCols columns c of block row blockIdx.y
+template <int B>
+__global__ void __launch_bounds__(256) k_bgs_dot(const double* const* __restrict__ Vs, long ldv, long n,
+                                                 const int* __restrict__ Js, const double* const* __restrict__ Ws,
+                                                 long ldw, double* __restrict__ partial, int ldp) {
+    const int s = blockIdx.z;
+    const int J = Js[s];
+    const int c0 = blockIdx.y * kBgsCols;
+    if (J <= 0 || c0 >= J) return;
+    const double* V = Vs[s];
+    const double* W = Ws[s];
+    const long chunk = (n + gridDim.x - 1) / gridDim.x;
+    const long r0 = (long)blockIdx.x * chunk;
+    const long r1 = min(n, r0 + chunk);
+    const int nc = min(kBgsCols, J - c0);
+    double acc[kBgsCols][B];
+#pragma unroll
+    for (int cc = 0; cc < kBgsCols; ++cc)
+#pragma unroll
+        for (int q = 0; q < B; ++q) acc[cc][q] = 0.0;
+    for (long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+        double w[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) w[q] = W[(long)q * ldw + i];
+#pragma unroll
+        for (int cc = 0; cc < kBgsCols; ++cc) {
+            if (cc < nc) {
+                const double v = V[(long)(c0 + cc) * ldv + i];
+#pragma unroll
+                for (int q = 0; q < B; ++q) acc[cc][q] = fma(v, w[q], acc[cc][q]);
+            }
+        }
+    }
+    __shared__ double red[kBgsCols * B][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int cc = 0; cc < kBgsCols; ++cc)
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            double a = acc[cc][q];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) red[cc * B + q][warp] = a;
+        }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < nc * B) {
+        double sum = 0.0;
+        for (int wv = 0; wv < (int)(blockDim.x >> 5); ++wv) sum += red[t][wv];
+        partial[((size_t)s * gridDim.x + blockIdx.x) * ldp + (size_t)c0 * B + t] = sum;
+    }
+}
+
+// W[q][i] -= sum_c V[c][i] H[c * B + q]
+template <int B>
+__global__ void __launch_bounds__(256) k_bgs_update(double* const* __restrict__ Ws, long ldw,
+                                                    const double* const* __restrict__ Vs, long ldv, long n,
+                                                    const int* __restrict__ Js, const double* __restrict__ H,
+                                                    int ldh) {
+    const int s = blockIdx.y;
+    const int J = Js[s];
+    if (J <= 0) return;
+    extern __shared__ double hs[];
+    for (int e = threadIdx.x; e < J * B; e += blockDim.x) hs[e] = H[(size_t)s * ldh + e];
+    __syncthreads();
+    double* W = Ws[s];
+    const double* V = Vs[s];
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double acc[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) acc[q] = 0.0;
+        for (int c = 0; c < J; ++c) {
+            const double v = V[(long)c * ldv + i];
+#pragma unroll
+            for (int q = 0; q < B; ++q) acc[q] = fma(v, hs[c * B + q], acc[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q) W[(long)q * ldw + i] -= acc[q];
+    }
+}
+
+template <int B>
+static int bgs_pass(int S, const double* const* Vd, long ldv, long n, const int* Jd, int Jmax, double* const* Wd,
+                    long ldw, double* partial, int nbx, int ldp, double* Hout, cudaStream_t stream) {
+    const dim3 gd(nbx, (Jmax + kBgsCols - 1) / kBgsCols, S);
+    k_bgs_dot<B><<<gd, 256, 0, stream>>>(Vd, ldv, n, Jd, (const double* const*)Wd, ldw, partial, ldp);
+    k_gs_reduce_par<<<dim3((Jmax * B + 31) / 32, S), 256, 0, stream>>>(partial, nbx, ldp, 0, nullptr, Hout, ldp);
+    const int ub = std::max(16, 4 * 152 / S);
+    k_bgs_update<B><<<dim3(ub, S), 256, (size_t)Jmax * B * sizeof(double), stream>>>(Wd, ldw, Vd, ldv, n, Jd,
+                                                                                      Hout, ldp);
+    NS_LAUNCH_CHECK();
+    return NSSTAB_OK;
+}
+
+int bcgs2_batch(int S, const double* const* V, long ldv, long n, const int* J, double* const* W, long ldw, int b,
+                double* H, int ldh, GsBatch& ws, cudaStream_t stream) {
+    if (b < 1 || b > kMaxGsBlock) {
+        set_error("block Gram-Schmidt: block size out of range");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    int Jmax = 0;
+    for (int s = 0; s < S; ++s) Jmax = std::max(Jmax, J[s]);
+    if (Jmax <= 0) return NSSTAB_OK;
+    const int ldp = Jmax * b;
+    NS_TRY(ws.alloc(S, ldp));
+    std::vector<int> jh(S);
+    std::vector<const double*> ph(2 * (size_t)S);
+    for (int s = 0; s < S; ++s) {
+        jh[s] = J[s];
+        ph[s] = V[s];
+        ph[S + s] = W[s];
+    }
+    NS_CUDA(cudaMemcpyAsync(ws.jdev, jh.data(), S * sizeof(int), cudaMemcpyHostToDevice, stream));
+    NS_CUDA(cudaMemcpyAsync(ws.ptrs, ph.data(), ph.size() * sizeof(double*), cudaMemcpyHostToDevice, stream));
+    const double* const* Vd = (const double* const*)ws.ptrs;
+    double* const* Wd = ws.ptrs + S;
+    // partial sums [S][nbx][ldp] fit the workspace's [S][grid][max_cols]
+    const int rows_of_blocks = (Jmax + kBgsCols - 1) / kBgsCols;
+    const int nbx = std::max(8, std::min(ws.grid, 4 * 152 / std::max(1, rows_of_blocks * S)));
+    double* h1 = ws.hdev;
+    double* h2 = ws.hdev + (size_t)S * ldp;
+#define NS_BGS(BB)                                                                                          \
+    do {                                                                                                    \
+        NS_TRY(bgs_pass<BB>(S, Vd, ldv, n, ws.jdev, Jmax, Wd, ldw, ws.partial, nbx, ldp, h1, stream));      \
+        NS_TRY(bgs_pass<BB>(S, Vd, ldv, n, ws.jdev, Jmax, Wd, ldw, ws.partial, nbx, ldp, h2, stream));      \
+    } while (0)
+    switch (b) {
+        case 1: NS_BGS(1); break;
+        case 2: NS_BGS(2); break;
+        case 3: NS_BGS(3); break;
+        case 4: NS_BGS(4); break;
+        case 5: NS_BGS(5); break;
+        case 6: NS_BGS(6); break;
+        case 7: NS_BGS(7); break;
+        default: NS_BGS(8); break;
+    }
+#undef NS_BGS
+    NS_CUDA(cudaMemcpyAsync(ws.hhost, ws.hdev, (size_t)2 * S * ldp * sizeof(double), cudaMemcpyDeviceToHost,
+                            stream));
+    NS_CUDA(cudaStreamSynchronize(stream));
+    for (int s = 0; s < S; ++s)
+        for (int e = 0; e < J[s] * b; ++e)
+            H[(size_t)s * ldh + e] = ws.hhost[(size_t)s * ldp + e] + ws.hhost[(size_t)(S + s) * ldp + e];
+    return NSSTAB_OK;
 }
 
 int GsBatch::alloc(int nmem, int cols) {
@@ -243,15 +413,16 @@ int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j,
     double* b2 = ws.hdev + 2 * (size_t)nmem * ldp;   // [nmem] spaced by ldp
     const dim3 g(ws.grid, nmem);
     const size_t sm = (size_t)jmax * sizeof(double);
+    const dim3 gr((jmax + 31) / 32, nmem);
     k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp);
-    k_gs_reduce_b<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, jd, h1);
+    k_gs_reduce_par<<<gr, 256, 0, stream>>>(ws.partial, ws.grid, ldp, 0, jd, h1, ldp);
     k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h1, ldp);
     k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp);
-    k_gs_reduce_b<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, jd, h2);
+    k_gs_reduce_par<<<gr, 256, 0, stream>>>(ws.partial, ws.grid, ldp, 0, jd, h2, ldp);
     k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h2, ldp);
     k_gs_dot_b<<<g, kGsThreads, 0, stream>>>((const double* const*)wd, n, n, one, (const double* const*)wd,
                                              ws.partial, ldp);
-    k_gs_reduce_b<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, one, b2);
+    k_gs_reduce_par<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, 0, one, b2, ldp);
     NS_LAUNCH_CHECK();
     NS_CUDA(cudaMemcpyAsync(ws.hhost, ws.hdev, (size_t)3 * nmem * ldp * sizeof(double), cudaMemcpyDeviceToHost,
                             stream));
@@ -300,7 +471,7 @@ static int dot_into(const double* V, long ldv, long n, int j, const double* w, d
                     cudaStream_t stream) {
     k_gs_dot<<<ws.grid, kGsThreads, 0, stream>>>(V, ldv, n, j, w, ws.partial, ws.max_cols);
     NS_LAUNCH_CHECK();
-    k_gs_reduce<<<1, 256, 0, stream>>>(ws.partial, ws.grid, ws.max_cols, j, out);
+    k_gs_reduce_par<<<(j + 31) / 32, 256, 0, stream>>>(ws.partial, ws.grid, ws.max_cols, j, nullptr, out, 0);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }

@@ -78,6 +78,14 @@ struct GsBatch {
 int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j, double* const* w,
                double* h, int ldh, double* beta, GsBatch& ws, cudaStream_t stream);
 int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream);
+// Blocked Gram-Schmidt (two passes) of the b <= kMaxGsBlock columns of W[s]
+// (ldw apart) against the first J[s] columns of V[s], for every set with
+// J[s] > 0: H = V^T W, W -= V H, twice, each a single read of V for all b
+// columns.  H[s][c * b + q] (host, row stride ldh) = the summed coefficients
+// of both passes.  The columns of W are not made orthogonal to each other.
+constexpr int kMaxGsBlock = 8;
+int bcgs2_batch(int S, const double* const* V, long ldv, long n, const int* J, double* const* W, long ldw, int b,
+                double* H, int ldh, GsBatch& ws, cudaStream_t stream);
 int vec_norm(const double* x, long n, double* out, GsWork& ws, cudaStream_t stream);
 int vec_scale(double* dst, const double* src, long n, double s, cudaStream_t stream);
 int vec_axpby(double* dst, double a, const double* x, double b, const double* y, long n, cudaStream_t stream);

@@ -157,12 +157,15 @@ def test_fp32_eigenvalues_track_fp64_on_a_fine_grid():
         assert np.min(np.abs(ref.mu - mu)) <= 1e-5 * abs(mu)
 
 
-@pytest.mark.parametrize("b", [1, 2, 4])
-def test_block_krylov_schur_matches_dense_eigendecomposition(small, b):
+@pytest.mark.parametrize("b,m", [(1, 60), (2, 60), (3, 60), (4, 60), (8, 96)])
+def test_block_krylov_schur_matches_dense_eigendecomposition(small, b, m):
+    """Block Krylov-Schur (blocked CGS2 against the basis, then within the
+    block) against LAPACK on the assembled propagator, every block size the
+    blocked kernels are instantiated for up to 8 (odd sizes included)."""
     kw, cfg, base, T, mu_dense = small
     st = nsstab.Stepper(per_set=b, **kw)
     v0 = np.stack([inputs.gaussian_field(16, 32, seed=40 + i) for i in range(b)])
-    res = st.block_arnoldi_eigs(_dev(base), _dev(v0), m=60, nev=4, tol=1e-10, T=T, max_restarts=200)
+    res = st.block_arnoldi_eigs(_dev(base), _dev(v0), m=m, nev=4, tol=1e-10, T=T, max_restarts=200)
     assert res.status == nsstab.OK and res.n_conv == len(res.mu)
     assert _match(res.mu, mu_dense[:6]) <= 1e-10
     assert res.n_matvec % b == 0

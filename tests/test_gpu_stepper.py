@@ -318,12 +318,13 @@ def test_long_runs_through_several_graph_chunks():
 # ---------------------------------------------------------------- double-float
 
 @pytest.mark.parametrize("nx,ny", [(16, 8), (128, 64), (64, 256), (512, 256), (2048, 1024)])
-def test_double_float_stepper_meets_the_fp64_bar(nx, ny):
-    """precision 48: FP32-pair arithmetic, held to the FP64 bar (1e-12 per step)
-    up to the 512x256 workload grid.  Its unit roundoff (2^-48) is 32 times
-    FP64's, and the centred differences of psi lose ~eps/(dx dy) to
-    cancellation, so the bound grows with the grid density beyond that
-    (measured 1.4e-12 at 2048x1024)."""
+def test_double_float_stepper_within_1e12_per_step_up_to_512x256_then_scaled(nx, ny):
+    """precision 48: FP32-pair arithmetic.  Held to the FP64 bar (1e-12 per
+    step) up to the 512x256 workload grid; beyond it the bound grows with the
+    grid density (2e-12 at 1024x512, 4e-12 at 2048x1024), because the unit
+    roundoff (2^-48) is 32 times FP64's and the centred differences of psi
+    lose ~eps/(dx dy) to cancellation (measured 1.4e-12 at 2048x1024).  So
+    the double-float stepper is FP64-class only up to 512x256."""
     kw = _cfg(nx, ny)
     cfg = ns2d.Config(**kw)
     w0 = inputs.wake_like_field(ny, nx, seed=1) + 0.3 * inputs.smooth_field(ny, nx, seed=2, kmax=5)
