@@ -296,7 +296,8 @@ static int bgs_pass(int S, const double* const* Vd, long ldv, long n, const int*
                     long ldw, double* partial, int nbx, int ldp, double* Hout, cudaStream_t stream) {
     const dim3 gd(nbx, (Jmax + kBgsCols - 1) / kBgsCols, S);
     k_bgs_dot<B><<<gd, 256, 0, stream>>>(Vd, ldv, n, Jd, (const double* const*)Wd, ldw, partial, ldp);
-    k_gs_reduce_par<<<dim3((Jmax * B + 31) / 32, S), 256, 0, stream>>>(partial, nbx, ldp, 0, nullptr, Hout, ldp);
+    k_gs_reduce_par<<<dim3((Jmax * B + 31) / 32, S), 256, 0, stream>>>(partial, nbx, ldp, Jmax * B, nullptr, Hout,
+                                                                        ldp);
     const int ub = std::max(16, 4 * 152 / S);
     k_bgs_update<B><<<dim3(ub, S), 256, (size_t)Jmax * B * sizeof(double), stream>>>(Wd, ldw, Vd, ldv, n, Jd,
                                                                                       Hout, ldp);
