@@ -254,6 +254,20 @@ int stepper_profile_linear(nsstab_stepper* st, const double* v, int nsteps, doub
  * (INVALID_ARG).  All synchronous. */
 int stepper_autotune(nsstab_stepper* st, int reps, int* plans);
 int stepper_set_plan(nsstab_stepper* st, int kernel, int log2_elems, int per_block);
+
+/* FP32 steppers: run each time step as four kernels instead of six, the two
+ * row passes (Sec. 3's nonlinear/linearised right-hand side, and the
+ * penalisation split) each fused into one pass that walks strips of
+ * rows_per_strip rows and keeps the neighbouring rows the centred y
+ * differences need in shared memory.  Same discrete operator, FP32
+ * rounding.  rows_per_strip = 0 selects the six-kernel step; otherwise it
+ * must be even and divide ny, and the grid must have 64 <= nx <= 2048
+ * (INVALID_ARG otherwise, also for FP64 and double-float steppers).
+ * Off by default.  With it on, stepper_profile_linear reports the fused
+ * passes in slots 2 (right-hand side) and 5 (penalisation) and 0 ms in
+ * slots 1 and 4.  Synchronous. */
+int stepper_set_fused_rows(nsstab_stepper* st, int rows_per_strip);
+int stepper_get_fused_rows(nsstab_stepper* st, int* rows_per_strip);
 int stepper_get_plan(nsstab_stepper* st, int kernel, int* log2_elems, int* per_block);
 
 /* arnoldi_eigs for every member of a batched stepper at once: member b runs

@@ -373,6 +373,20 @@ int stepper_get_plan(nsstab_stepper* st, int kernel, int* log2_elems, int* per_b
     return NSSTAB_OK;
 }
 
+int stepper_set_fused_rows(nsstab_stepper* st, int rows_per_strip) {
+    if (!st) return bad_arg("stepper_set_fused_rows: null stepper");
+    if (rows_per_strip < 0) return bad_arg("stepper_set_fused_rows: rows_per_strip must be >= 0");
+    const int rc = st->impl->set_fused_rows(rows_per_strip);
+    if (rc == NSSTAB_OK) cudaStreamSynchronize(st->stream);
+    return rc;
+}
+
+int stepper_get_fused_rows(nsstab_stepper* st, int* rows_per_strip) {
+    if (!st || !rows_per_strip) return bad_arg("stepper_get_fused_rows: null argument");
+    *rows_per_strip = st->impl->fused_rows();
+    return NSSTAB_OK;
+}
+
 int cgs2_orthogonalize(const double* V, long ldv, long n, int j, double* w, double* h, double* beta, void* stream) {
     if (!w || !beta || (j > 0 && (!V || !h))) return bad_arg("cgs2_orthogonalize: null argument");
     if (n < 1 || j < 0 || j > 4096 || (j > 0 && ldv < n)) return bad_arg("cgs2_orthogonalize: bad sizes");

@@ -196,13 +196,14 @@ __device__ __forceinline__ void stockham_pass(Cx<T>* d, int q, int lq, int logN,
     __syncthreads();
 }
 
-// In-place transform of nseq sequences (see file comment).  All threads of
-// the block must call it.  Every thread owns E = 2^LE elements per pass:
-// radix-E passes, then one smaller radix for the remaining factors.
-// Requirements: logN >= LE; blockDim.x * E is a multiple of N; tw is the
-// twiddle table of this N and LE (twiddle_table_len entries).
-template <bool INV, class T, int LE>
-__device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __restrict__ tw) {
+// In-place transform of nseq sequences, sequence f at seq(f) (a device
+// functor returning its shared-memory start).  All threads of the block must
+// call it.  Every thread owns E = 2^LE elements per pass: radix-E passes,
+// then one smaller radix for the remaining factors.  Requirements: logN >=
+// LE; blockDim.x >= N/E; tw is the twiddle table of this N and LE
+// (twiddle_table_len entries).
+template <bool INV, class T, int LE, class SeqPtr>
+__device__ void fft_smem_seqs(SeqPtr seq, int logN, int nseq, const Cx<T>* __restrict__ tw) {
     const int t = threadIdx.x;
     const int lq = logN - LE;                   // log2(N/E): threads per sequence
     const int q = t & ((1 << lq) - 1);
@@ -210,7 +211,7 @@ __device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __res
     for (int f0 = 0; f0 < nseq; f0 += F) {
         const int f = f0 + (t >> lq);
         const bool act = f < nseq;
-        Cx<T>* d = s + (size_t)(act ? f : 0) * S;
+        Cx<T>* d = seq(act ? f : 0);
         int nsl = 0;
         int rem = logN;
         const Cx<T>* twp = tw;   // start of this pass's rows
@@ -223,6 +224,13 @@ __device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __res
         if (LE == 3 && rem == 2) stockham_pass<INV, T, LE, (LE == 3 ? 2 : 1)>(d, q, lq, logN, nsl, twp, act);
         if (rem == 1) stockham_pass<INV, T, LE, 1>(d, q, lq, logN, nsl, twp, act);
     }
+}
+
+// In-place transform of nseq sequences stored S elements apart from s (see
+// the file comment and fft_smem_seqs).  blockDim.x * E is a multiple of N.
+template <bool INV, class T, int LE>
+__device__ void fft_smem(Cx<T>* s, int logN, int S, int nseq, const Cx<T>* __restrict__ tw) {
+    fft_smem_seqs<INV, T, LE>([=](int f) { return s + (size_t)f * S; }, logN, nseq, tw);
 }
 
 }  // namespace nsstab

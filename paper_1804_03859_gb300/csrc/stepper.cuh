@@ -42,6 +42,10 @@ struct StepperBase {
     virtual int autotune(int reps, int* chosen) = 0;
     virtual int plan_of(int kid, int* le, int* per) const = 0;
     virtual int set_plan(int kid, int le, int per) = 0;
+    // FP32 steppers: run the two row passes of a step as fused kernels over
+    // strips of R rows (rowroll.cuh); R = 0 returns to the six-kernel step
+    virtual int set_fused_rows(int R) = 0;
+    virtual int fused_rows() const = 0;
 };
 
 constexpr int kNumStepKernels = 6;   // col_poisson, row_inverse(psi), row_forward(rhs),

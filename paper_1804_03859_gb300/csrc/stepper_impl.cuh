@@ -80,6 +80,8 @@ template <class T> struct Fields {
     const T* Ub; const T* Vb; const T* DxOb; const T* DyOb;   // base-derived fields
     Cx<T>* X1; Cx<T>* X2;  // x-spectral, y-physical [kx][y]
     Cx<T>* X3;             // x-spectrum of v (kVel steppers)
+    Cx<T>* X4;             // x-spectrum of N written by the fused row pass (FP32)
+    const Cx<T>* XN;       // x-spectrum of N read by k_col_update (X1, or X4)
     Cx<T>* Wh; Cx<T>* Nh;  // full spectra [kx][ky]
     const T* tA; const T* tB; const T* tP;   // spectral operator tables [nxh+1][ny]
     const T* tDx; const T* tDy;              // sin(2 pi kx/nx)/dx [nxh+1], sin(2 pi ky/ny)/dy [ny]
@@ -99,10 +101,12 @@ template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
     if (f.Y) f.Y += fo;
     f.X1 += co;
     f.X2 += co;
+    f.XN += co;
     if (kF32<T>) {
         f.U += fo;
         f.V += fo;
         f.X3 += co;
+        f.X4 += co;
     }
     f.Wh += co;
     f.Nh += co;
@@ -442,7 +446,8 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     }
 }
 
-// Forward y-transform of N (x-spectra in X1); AB2/AB1 + Crank-Nicolson update
+// Forward y-transform of N (x-spectra in XN: X1, or X4 after the fused FP32
+// row pass); AB2/AB1 + Crank-Nicolson update
 //   omega*^ = tA omega^ + tB (c1 N^n + c0 N^{n-1}),  psi*^ = tP omega*^
 // (tA, tB carry the 1/(nx ny) of the inverse transform); Nh <- N^n; inverse
 // y-transforms of omega*^ -> X1 and psi*^ -> X2 (kVel: u*'^ -> X2 and
@@ -470,7 +475,7 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
         for (int it = 0; it < E; ++it) {
             if (it >= EL) continue;
             const size_t g = (size_t)c0i * ny + threadIdx.x + it * blockDim.x;
-            a[it] = f.X1[g];
+            a[it] = f.XN[g];
             b[it] = f.Wh[g];
             if (!first) c3[it] = f.Nh[g];
         }
@@ -631,6 +636,12 @@ __global__ void k_diff_sumsq(const T* __restrict__ a, const T* __restrict__ b, s
     }
 }
 
+}  // namespace nsstab
+
+#include "rowroll.cuh"   // fused FP32 row passes (uses Fields, row modes and the FFT above)
+
+namespace nsstab {
+
 // ------------------------------------------------------------- host side
 
 // One launch configuration: `per` sequences (row pairs or columns) per
@@ -691,7 +702,7 @@ class StepperImpl : public StepperBase {
     int residual(const double* q, double* r) override;
     int sfd(double* omega, double chi, double Delta, double tol, long max_steps, int check_every,
             double* r, long* steps) override;
-    int launches_per_step() const override { return kNumStepKernels; }
+    int launches_per_step() const override { return rollR_ ? 4 : kNumStepKernels; }
     int profile_linear(const double* v, int nsteps, double* ms) override;
     int autotune(int reps, int* chosen) override;
     int plan_of(int kid, int* le, int* per) const override {
@@ -701,6 +712,8 @@ class StepperImpl : public StepperBase {
         return NSSTAB_OK;
     }
     int set_plan(int kid, int le, int per) override;
+    int set_fused_rows(int R) override;
+    int fused_rows() const override { return rollR_; }
 
   private:
     nsstab_config cfg_;
@@ -719,6 +732,7 @@ class StepperImpl : public StepperBase {
     unsigned char* active_ = nullptr;
     unsigned char* tmask_ = nullptr;               // device {1, 0, 0, 1}: member 0 alone, member 1 alone
     const unsigned char* act_override_ = nullptr;  // mask for the next launches (null: the stepper's own)
+    bool xn_x4_ = false;                           // k_col_update reads N from X4 (fused row passes)
     std::vector<unsigned char> active_host_;
     const double** ptr_in_ = nullptr;   // device arrays of B member pointers
     double** ptr_out_ = nullptr;
@@ -726,6 +740,8 @@ class StepperImpl : public StepperBase {
     std::vector<double*> pout_host_;
     bool have_base_ = false;
     Launch plan_[kNumStepKernels];
+    int rollR_ = 0;                // fused FP32 row passes over strips of rollR_ rows (0: six-kernel step)
+    RollShape rs_{};
     T scale_ = T(1);
     struct GraphKey {
         int nsteps, flags;
@@ -772,6 +788,8 @@ class StepperImpl : public StepperBase {
     int gather_contig(const double* src, int count);     // members 0..count-1 from [count][n]
     int scatter_contig(const T* from, double* dst);      // all members to [B][n]
     int launch(int kid, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool first);
+    int launch_roll(bool pen, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool write_w);
+    RollShape roll_shape(int R) const;
     int launch_plain(cudaStream_t st);
     int transform_W();                                   // X1 = x-spectrum of W
     int stream_function(cudaStream_t st);                // Wh, X2 (X3), P (U, V) from X1
@@ -978,6 +996,7 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
             break;
         }
         case KCOLU: {
+            if (xn_x4_) fl.XN = f_.X4;
             const T c1 = first ? T(1) : T(1.5), c0 = first ? T(0) : T(-0.5);
 #define CALL_COLU(le) k_col_update<T, le><<<g, L.threads, L.smem, st>>>(fl, L.per, c1, c0, first)
             NS_DISPATCH_LE(L, CALL_COLU);
@@ -1001,6 +1020,69 @@ template <class T> int StepperImpl<T>::launch(int kid, cudaStream_t st, bool lin
     }
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
+}
+
+// Shape of the fused row passes for strips of R rows (nunits = 0: the grid
+// or arithmetic does not allow it).
+template <class T> RollShape StepperImpl<T>::roll_shape(int R) const {
+    RollShape r{};
+    if (!kF32<T> || nx_ < 64 || nx_ > kRollPoints || R < 2 || (R & 1) || R > ny_ || ny_ % R != 0) return r;
+    r.R = R;
+    r.G = std::min(kRollPoints / nx_, ny_ / R);
+    r.upm = ny_ / (R * r.G);
+    r.nunits = B_ * r.upm;
+    return r;
+}
+
+template <class T> int StepperImpl<T>::set_fused_rows(int R) {
+    if (R == 0) {
+        rollR_ = 0;
+        clear_graphs();
+        return NSSTAB_OK;
+    }
+    const RollShape r = roll_shape(R);
+    if (r.nunits == 0) {
+        set_error("fused row passes need the FP32 stepper, 64 <= nx <= 2048 and an even R dividing ny");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    if constexpr (kF32<T>) {
+        const int sm = 96 * kRollPoints;
+        NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_RHS_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_RHS_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_PEN_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+        NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_PEN_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+    }
+    rollR_ = R;
+    rs_ = r;
+    clear_graphs();
+    return NSSTAB_OK;
+}
+
+// One fused row pass over every active member: persistent blocks, one per
+// SM at most (the pass holds 96 G nx bytes of shared memory).
+template <class T>
+int StepperImpl<T>::launch_roll(bool pen, cudaStream_t st, bool linear, bool sfd, bool do_fft, bool write_w) {
+    if constexpr (kF32<T>) {
+        RollShape r = rs_;
+        r.write_w = write_w ? 1 : 0;
+        r.do_fft = do_fft ? 1 : 0;
+        Fields<T> fl = f_;
+        if (act_override_) fl.active = act_override_;
+        const int blocks = std::min(r.nunits, 152);
+        const size_t smem = (size_t)96 * r.G * nx_;
+        if (!pen) {
+            if (linear) k_row_roll<FWD_RHS_LIN><<<blocks, kRollThreads, smem, st>>>(fl, r, false);
+            else k_row_roll<FWD_RHS_NL><<<blocks, kRollThreads, smem, st>>>(fl, r, false);
+        } else {
+            if (linear) k_row_roll<FWD_PEN_LIN><<<blocks, kRollThreads, smem, st>>>(fl, r, sfd);
+            else k_row_roll<FWD_PEN_NL><<<blocks, kRollThreads, smem, st>>>(fl, r, sfd);
+        }
+        NS_LAUNCH_CHECK();
+        return NSSTAB_OK;
+    } else {
+        set_error("fused row passes exist for the FP32 stepper only");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
 }
 
 // --------------------------------------------------------------- tables
@@ -1165,6 +1247,10 @@ template <class T> int StepperImpl<T>::init() {
         NS_TRY(dalloc(&U, B * n_));
         NS_TRY(dalloc(&V, B * n_));
         NS_TRY(dalloc(&X3, B * nc_));
+        C* X4;
+        NS_TRY(dalloc(&X4, B * nc_));
+        f_.X4 = X4;
+        NS_CUDA(cudaMemsetAsync(X4, 0, B * nc_ * sizeof(C), stream_));
         NS_TRY(dalloc(&tDx, (size_t)nxh_ + 1));
         NS_TRY(dalloc(&tDy, (size_t)ny_));
         f_.U = U; f_.V = V; f_.X3 = X3; f_.tDx = tDx; f_.tDy = tDy;
@@ -1188,6 +1274,7 @@ template <class T> int StepperImpl<T>::init() {
     NS_CUDA(cudaMallocHost((void**)&red_host_, B * kRedBlocks * sizeof(double)));
     f_.W = W; f_.P = P; f_.cS = cS; f_.cG = cG;
     f_.X1 = X1; f_.X2 = X2; f_.Wh = Wh; f_.Nh = Nh;
+    f_.XN = X1;
     f_.tA = tA; f_.tB = tB; f_.tP = tP;
     f_.Y = nullptr;
     f_.Ub = f_.Vb = f_.DxOb = f_.DyOb = nullptr;
@@ -1210,6 +1297,7 @@ template <class T> int StepperImpl<T>::init() {
         }
         NS_TRY(set_plan_tm(k, L.le, L.per, L.tm));
     }
+
     NS_CUDA(cudaStreamSynchronize(stream_));
     return NSSTAB_OK;
 }
@@ -1315,6 +1403,21 @@ int StepperImpl<T>::issue_steps(cudaStream_t st, int nsteps, bool linear, bool s
             if (rc == NSSTAB_OK) rc = launch(KFWDP, st, true, false, fft, first);
             act_override_ = nullptr;
             NS_TRY(rc);
+        }
+        return NSSTAB_OK;
+    }
+    if (rollR_) {
+        // four kernels: column Poisson pass, fused RHS row pass, column
+        // update, fused penalisation row pass (omega to W on the last step)
+        for (int s = 0; s < nsteps; ++s) {
+            const bool first = first_ab1 && s == 0;
+            NS_TRY(launch(KCOLP, st, false, false, true, first));
+            NS_TRY(launch_roll(false, st, linear, false, true, false));
+            xn_x4_ = true;
+            const int rc = launch(KCOLU, st, linear, false, true, first);
+            xn_x4_ = false;
+            NS_TRY(rc);
+            NS_TRY(launch_roll(true, st, linear, sfd, fft_last || (s + 1 < nsteps), s + 1 == nsteps));
         }
         return NSSTAB_OK;
     }
@@ -1442,7 +1545,15 @@ template <class T> int StepperImpl<T>::profile_linear(const double* v, int nstep
         const bool first = (s == 0);
         for (int k = 0; k < kNumStepKernels && rc == NSSTAB_OK; ++k) {
             cudaEventRecord(ev[k], stream_);
-            rc = launch(k, stream_, true, false, true, first);
+            if (!rollR_) rc = launch(k, stream_, true, false, true, first);
+            else if (k == KCOLP) rc = launch(k, stream_, true, false, true, first);
+            else if (k == KCOLU) {
+                xn_x4_ = true;
+                rc = launch(k, stream_, true, false, true, first);
+                xn_x4_ = false;
+            }
+            else if (k == KFWDR) rc = launch_roll(false, stream_, true, false, true, false);
+            else if (k == KFWDP) rc = launch_roll(true, stream_, true, false, true, s + 1 == nsteps);
         }
         cudaEventRecord(ev[kNumStepKernels], stream_);
         if (rc != NSSTAB_OK) break;

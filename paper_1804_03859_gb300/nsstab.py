@@ -98,6 +98,8 @@ SIGNATURES = [
     ("stepper_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip]),
     ("stepper_set_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     ("stepper_get_plan", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, _ip, _ip]),
+    ("stepper_set_fused_rows", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("stepper_get_fused_rows", ctypes.c_int, [ctypes.c_void_p, _ip]),
     ("block_arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp,
                                           _dp, ctypes.c_void_p, _ip, _ip, _ip]),
@@ -602,6 +604,16 @@ class Stepper:
         _check(self._lib.stepper_get_plan(self._h, int(kernel), ctypes.byref(le), ctypes.byref(per)),
                "stepper_get_plan")
         return le.value, per.value
+
+    def stepper_set_fused_rows(self, rows_per_strip: int):
+        """FP32: four-kernel step with fused row passes over strips of
+        rows_per_strip rows (0: the six-kernel step)."""
+        _check(self._lib.stepper_set_fused_rows(self._h, int(rows_per_strip)), "stepper_set_fused_rows")
+
+    def stepper_get_fused_rows(self) -> int:
+        r = ctypes.c_int()
+        _check(self._lib.stepper_get_fused_rows(self._h, ctypes.byref(r)), "stepper_get_fused_rows")
+        return r.value
 
     def plans(self) -> dict:
         return {k: self.stepper_get_plan(i) for i, k in enumerate(self.KERNELS)}
