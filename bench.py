@@ -160,6 +160,20 @@ def job_value(world: int, steps: int, pts_per_step: int, elapsed_max: float) -> 
     return world * steps * pts_per_step / elapsed_max
 
 
+def share_of(items: list, rank: int, world: int) -> list:
+    """Rank `rank`'s share of independent units (Reynolds numbers of a sweep,
+    solves of a serving batch): every world-th one, starting at rank.  The
+    units need no exchange, so the shares run with no collective."""
+    return items[rank::world]
+
+
+def replica_command(argv: list, gpus: int, port: int) -> list:
+    """The command that runs this benchmark as `gpus` ranks of one node (one
+    process per GPU) when it was started as a single process."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -240,6 +254,84 @@ def cpu_oracle_sample(nsteps_sample: int = 20, seed: int = 0):
     return nsteps_sample * NX * NY, el
 
 
+def _oracle_worker(nsteps, seed, barrier, out):
+    barrier.wait()
+    t0 = time.time()
+    pts, _ = cpu_oracle_sample(nsteps, seed=seed)
+    out.put((pts, t0, time.time()))
+
+
+def cpu_oracle_all_cores(nsteps_sample: int = 10, procs: int | None = None):
+    """The oracle on every host core at once: `procs` independent processes
+    (spawned; numpy single-threaded in each), each running the bounded sample
+    of cpu_oracle_sample on its own seed, started together.  Returns (grid-pt
+    steps of all processes, wall seconds from the first start to the last
+    end, processes)."""
+    import multiprocessing as mpc
+
+    procs = procs or os.cpu_count() or 1
+    ctx = mpc.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    q = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(nsteps_sample, 100 + i, barrier, q)) for i in range(procs)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=600) for _ in ps]
+    for p in ps:
+        p.join(timeout=60)
+    pts = sum(r[0] for r in res)
+    return pts, max(r[2] for r in res) - min(r[1] for r in res), procs
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+C1 = dict(nx=128, ny=64, dt=0.01, Re=50.0, T=0.5, m=64, nev=4, tol=1e-8)
+
+
+def cpu_oracle_c1_eigs(max_restarts: int = 6):
+    """Time to the leading 4 eigenvalues of the 128x64 cylinder case (Re 50,
+    T 0.5, Krylov-Schur m 64, tol 1e-8) with the oracle on one core, about a
+    synthetic developed-wake base (inputs.wake_like_field, seed 0)."""
+    from oracle import krylov, ns2d
+    from paper_1804_03859_gb300 import inputs
+
+    cfg = ns2d.Config(nx=C1["nx"], ny=C1["ny"], dt=C1["dt"], Re=C1["Re"])
+    base = ns2d.Base.from_omega(inputs.wake_like_field(C1["ny"], C1["nx"], seed=0), cfg)
+    v0 = inputs.gaussian_field(C1["ny"], C1["nx"], seed=1)
+    mv = lambda x: ns2d.apply_expTL(base, x.reshape(C1["ny"], C1["nx"]), C1["T"], cfg).ravel()
+    t0 = time.perf_counter()
+    e = krylov.krylov_schur(mv, v0, m=C1["m"], nev=C1["nev"], tol=C1["tol"], max_restarts=max_restarts)
+    return {"seconds": time.perf_counter() - t0, "n_matvec": e.n_matvec, "n_conv": e.n_conv,
+            "n_eig": len(e.mu), "mu": [[float(m.real), float(m.imag)] for m in e.mu], "cores": 1}
+
+
+def golden_c2():
+    """The oracle's leading eigenvalues of the 512x256 case (written by
+    tests/golden/make_c2_eigs.py), or None."""
+    try:
+        d = json.load(open(os.path.join(ROOT, "tests", "golden", "c2_eigs_512x256.json")))
+    except Exception:
+        return None
+    d["mu"] = np.array([complex(a, b) for a, b in d["eigenvalues"]])
+    return d
+
+
+def err_vs(ref_mu, mu):
+    """Relative distance of each of mu to the nearest of ref_mu."""
+    return [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in mu]
+
+
 # -------------------------------------------------------------- reference
 
 def run_reference(args, rank: int):
@@ -269,7 +361,27 @@ def run_reference(args, rank: int):
 
 # ----------------------------------------------------------------- native
 
+def cpu_legs(args):
+    """The CPU oracle timed on the host (rank 0): one core on a bounded sample
+    of the bench step, every core at once (independent processes), and the
+    128x64 case's time to its leading eigenvalues.  Run before any GPU work."""
+    pts, el = cpu_oracle_sample(20)
+    apts, ael, nproc = cpu_oracle_all_cores(10)
+    c1 = cpu_oracle_c1_eigs()
+    model = cpu_model()
+    return {"value": pts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "20 of the 200 linearised steps of one M v plus one CGS2 vs 64 vectors at 512x256, "
+                      "numpy FP64 on one host core",
+            "cpu_model": model, "cpu_count": os.cpu_count(),
+            "all_cores": {"value": apts / ael, "unit": UNIT, "cores": nproc, "kind": "oracle",
+                          "sample": f"{nproc} processes at once, each 10 of the 200 linearised steps of one M v "
+                                    "plus one CGS2 vs 64 vectors at 512x256 (numpy FP64, one thread each)"},
+            "time_to_eigs_128x64": c1}
+
+
 def run_native(args, rank: int, world: int):
+    cpu = cpu_legs(args) if (rank == 0 and not args.no_cpu) else None
+
     import torch
 
     from paper_1804_03859_gb300 import build, inputs, nsstab
@@ -383,24 +495,34 @@ def run_native(args, rank: int, world: int):
     ms48 = st48.stepper_profile_linear(v0, prof_steps)
     step_flops = sum(fl.values())
 
+    # steady base flow of this workload (Newton-Krylov), about which the
+    # eigen-solves below run
+    newton_leg, qbase = (None, None) if (args.no_serve or args.no_eigs) else newton_leg_run(args, dev)
+    eig_base = qbase if qbase is not None else base
+    gold = golden_c2()
+
     # time to the leading eigenvalues (Krylov-Schur, m = 128, nev = 8)
     eigs = None
     if not args.no_eigs:
-        eigs = {}
+        eigs = {"base_flow": "Newton-Krylov steady state, r <= 1e-10" if qbase is not None else
+                "synthetic developed-wake field",
+                "oracle_reference": None if gold is None else
+                "tests/golden/c2_eigs_512x256.json (CPU oracle: Newton base flow, Krylov-Schur m 128, tol 1e-10)"}
         ref_mu = None
         for prec, st, tol in ((64, st64, 1e-8), (48, st48, 1e-8), (32, st32, TOL32)):
+            st.stepper_set_base(eig_base)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            r = st.arnoldi_eigs(None, v0, m=KRYLOV_M, nev=NEV, tol=tol, T=T_SAMPLE, max_restarts=4)
+            r = st.arnoldi_eigs(None, v0, m=KRYLOV_M, nev=NEV, tol=tol, T=T_SAMPLE, max_restarts=8)
             el = time.perf_counter() - t0
             d = {"seconds": el, "n_matvec": r.n_matvec, "n_conv": r.n_conv, "n_eig": len(r.mu), "tol": tol,
                  "leading_mu": [r.mu[0].real, r.mu[0].imag]}
             if prec == 64:
                 ref_mu = r.mu
             elif ref_mu is not None:
-                d["abs_err_vs_fp64"] = [float(np.min(np.abs(ref_mu - m))) for m in r.mu]
-                errs = [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in r.mu]
-                d["rel_err_vs_fp64"] = errs
+                d["rel_err_vs_fp64_gpu"] = err_vs(ref_mu, r.mu)
+            if gold is not None and qbase is not None:
+                d["rel_err_vs_oracle"] = err_vs(gold["mu"], r.mu)
             eigs[f"fp{prec}"] = d
         # the same eigenproblem with a block of 2 vectors per product with M
         # and twice the basis (block Krylov-Schur; the batched stepper runs
@@ -411,7 +533,7 @@ def run_native(args, rank: int, world: int):
                 stb2.stepper_autotune(reps=3)
             v2 = torch.from_numpy(np.stack([inputs.gaussian_field(NY, NX, seed=400 + i) for i in range(2)])).to(dev)
             v2[0].copy_(v0)
-            stb2.stepper_set_base(base)
+            stb2.stepper_set_base(eig_base)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             r = stb2.block_arnoldi_eigs(None, v2, m=2 * KRYLOV_M, nev=NEV, tol=1e-8, T=T_SAMPLE, max_restarts=8)
@@ -419,7 +541,9 @@ def run_native(args, rank: int, world: int):
             d = {"seconds": el, "n_matvec": r.n_matvec, "n_conv": r.n_conv, "n_eig": len(r.mu), "tol": 1e-8,
                  "block": 2, "krylov_m": 2 * KRYLOV_M, "leading_mu": [r.mu[0].real, r.mu[0].imag]}
             if ref_mu is not None:
-                d["rel_err_vs_fp64"] = [float(np.min(np.abs(ref_mu - m)) / abs(m)) for m in r.mu]
+                d["rel_err_vs_fp64_gpu"] = err_vs(ref_mu, r.mu)
+            if gold is not None and qbase is not None:
+                d["rel_err_vs_oracle"] = err_vs(gold["mu"], r.mu)
             eigs[f"fp{prec}_block2"] = d
             del stb2
 
@@ -429,12 +553,14 @@ def run_native(args, rank: int, world: int):
     batched = None
     if not args.no_batch:
         nb = 16
-        Res = [float(x) for x in np.linspace(40.0, 100.0, nb)]
+        Res_all = [float(x) for x in np.linspace(40.0, 100.0, nb)]
+        mine = share_of(list(range(nb)), rank, world)   # this rank's Reynolds numbers (no exchange)
+        Res = [Res_all[k] for k in mine]
         stb = nsstab.Stepper(nx=NX, ny=NY, dt=DT, Re=Res, precision=32)
         if not args.no_tune:
             stb.stepper_autotune(reps=3)
-        bases = torch.from_numpy(np.stack([inputs.wake_like_field(NY, NX, seed=k) for k in range(nb)])).to(dev)
-        vb = torch.from_numpy(np.stack([inputs.gaussian_field(NY, NX, seed=100 + k) for k in range(nb)])).to(dev)
+        bases = torch.from_numpy(np.stack([inputs.wake_like_field(NY, NX, seed=k) for k in mine])).to(dev)
+        vb = torch.from_numpy(np.stack([inputs.gaussian_field(NY, NX, seed=100 + k) for k in mine])).to(dev)
         wb = torch.empty_like(vb)
         stb.stepper_set_base(bases)
         for _ in range(args.warmup):
@@ -451,8 +577,9 @@ def run_native(args, rank: int, world: int):
             e1.synchronize()
             tb += e0.elapsed_time(e1) / 1e3
         tb = max_over_ranks(tb, dev)
-        batched = {"members": nb, "Re": [Res[0], Res[-1]], "precision": "f32",
-                   "value": job_value(world, args.steps, nb * pts_per_step, tb), "unit": UNIT,
+        batched = {"members": nb, "Re": [Res_all[0], Res_all[-1]], "precision": "f32",
+                   "members_per_rank": len(mine), "partition": "Reynolds numbers split across ranks, no collective",
+                   "value": args.steps * nb * pts_per_step / tb, "unit": UNIT,
                    "ms_per_step": 1e3 * tb / args.steps, "plans": stb.plans()}
         if not args.no_eigs:
             torch.cuda.synchronize()
@@ -474,18 +601,12 @@ def run_native(args, rank: int, world: int):
         serving = serve_leg(args, dev)
     bblock = None if (args.no_batch or world > 1) else batched_block_leg(args, dev)
     unet_leg = None if args.no_serve else unet_train_leg(args, dev)
-    newton_leg = None if (args.no_serve or args.no_eigs) else newton_leg_run(args, dev)
     wake_leg = None if (args.no_serve or args.no_eigs) else wake_stability_leg(args, dev)
+    c1_leg = None if args.no_eigs else c1_gpu_leg(dev)
 
     if rank != 0:
         return
     clocks = clk.summary()
-    cpu = None
-    if not args.no_cpu:
-        pts, el = cpu_oracle_sample(20)
-        cpu = {"value": pts / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "20 of the 200 linearised steps of one M v plus one CGS2 vs 64 vectors at 512x256, "
-                         "numpy FP64 on one host core"}
     per_step_launches = 1 + 6 * nsteps + 8
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -498,6 +619,7 @@ def run_native(args, rank: int, world: int):
                    "parallelism": "replicas" if world > 1 else "single",
                    "launch_plans": plans},
         "roofline": roofline,
+        "roofline_hbm": (bblock or {}).get("roofline_hbm"),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": args.steps * per_step_launches,
@@ -516,6 +638,9 @@ def run_native(args, rank: int, world: int):
         "unet": unet_leg,
         "newton": newton_leg,
         "wake_stability": wake_leg,
+        "time_to_eigs_128x64": None if c1_leg is None else {
+            "workload": "cylinder 128x64, Re 50, T 0.5, Krylov-Schur m 64, leading 4 at 1e-8, synthetic wake base",
+            "gpu": c1_leg, "oracle_one_core": (cpu or {}).get("time_to_eigs_128x64")},
     }
     print(json.dumps(out))
 
@@ -572,7 +697,9 @@ def batched_block_leg(args, dev, rate_grid=(2048, 1024), rate_block=8, rate_step
                        "reps": reps, "value": fields * nx * ny * rate_steps / sec, "unit": UNIT,
                        "ms_per_step_all_fields": 1e3 * sec / rate_steps,
                        "seconds_per_round_at_T_0_5": sec * round(0.5 / dt) / rate_steps,
-                       "l2": "inputs far larger than L2 (128 fields x 2M points)", "plans": st.plans()}
+                       "l2": "inputs far larger than L2 (128 fields x 2M points)", "plans": st.plans(),
+                       "fused_rows": st.stepper_get_fused_rows()}
+        out["roofline_hbm"] = hbm_roofline(st, v, fields * nx * ny)
         del st, v, w
         torch.cuda.empty_cache()
     if eig_grid is not None and not args.no_eigs:
@@ -620,6 +747,32 @@ def batched_block_leg(args, dev, rate_grid=(2048, 1024), rate_block=8, rate_step
     return out
 
 
+ALG_BYTES_FP32_LIN = 24     # per grid-point step: read omega, N^{n-1}, Psi_b, Omega_b; write omega, N^n (FP32)
+
+
+def hbm_roofline(st, v, pts: int, nsteps: int = 4):
+    """HBM roofline of one linearised FP32 time step over a batch far larger
+    than L2: the step's algorithmic bytes (24 B per grid point) over the
+    step's live duration (CUDA events on the stepper's stream around each
+    kernel, summed), against the measured copy bandwidth; with the DRAM bytes
+    per grid point of the committed ncu capture of the same step, if it was
+    taken on the current kernel sources."""
+    ms = st.stepper_profile_linear(v, nsteps)
+    step_s = sum(ms.values()) / nsteps / 1e3
+    peak = peaks().get("hbm_gbs")
+    achieved = ALG_BYTES_FP32_LIN * pts / step_s / 1e9
+    dom = max(ms, key=ms.get)
+    tr = load_traffic("fp32_step_2048x1024_b128_bytes_per_pt")
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if peak else None,
+            "traffic": None if tr is None else tr * pts,
+            "traffic_bytes_per_pt": tr, "algorithmic_bytes_per_pt": ALG_BYTES_FP32_LIN,
+            "scope": "one whole linearised step (all kernels) of 128 FP32 fields at 2048x1024",
+            "ms_per_step": 1e3 * step_s, "dominant_kernel": dom,
+            "kernel_ms": {k: x / nsteps for k, x in ms.items()},
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
+
+
 def newton_leg_run(args, dev):
     """Steady base flow of the bench workload (512x256, Re 60) by
     Newton-Krylov: FP64 nonlinear map and residual, Jacobian products by the
@@ -641,10 +794,37 @@ def newton_leg_run(args, dev):
     rc, r, it, mv = st.newton_krylov_fixedpoint(q, T=0.4, gmres_m=50, tol=1e-10, max_newton=30, lin=lin)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    return {"workload": f"steady base flow {NX}x{NY}, Re {RE}", "T": 0.4, "gmres_m": 50, "tol": 1e-10,
-            "jacobian": "exact tangent (co-integrated), f32", "start": "300 SFD steps from rest (chi 0.1, Delta 0.5)",
-            "status": rc, "residual": r, "newton_iters": it, "jacobian_products": mv, "sfd_seconds": t1 - t0,
-            "newton_seconds": t2 - t1}
+    out = {"workload": f"steady base flow {NX}x{NY}, Re {RE}", "T": 0.4, "gmres_m": 50, "tol": 1e-10,
+           "jacobian": "exact tangent (co-integrated), f32", "start": "300 SFD steps from rest (chi 0.1, Delta 0.5)",
+           "status": rc, "residual": r, "newton_iters": it, "jacobian_products": mv, "sfd_seconds": t1 - t0,
+           "newton_seconds": t2 - t1}
+    gold = golden_c2()
+    if gold is not None:
+        qh = q.cpu().numpy()
+        smp = gold["base_flow"]["samples"]
+        out["max_sample_diff_vs_oracle"] = float(max(abs(qh[j, i] - v) for j, i, v in smp))
+    return out, (q if rc == nsstab.OK else None)
+
+
+def c1_gpu_leg(dev):
+    """The 128x64 case's time to its leading 4 eigenvalues on the GPU (FP64
+    stepper, Krylov-Schur m 64, tol 1e-8) about the same synthetic base as
+    the oracle's timing in the CPU baseline, and the eigenvalues' distance
+    to the oracle's."""
+    import torch
+
+    from paper_1804_03859_gb300 import inputs, nsstab
+
+    st = nsstab.Stepper(nx=C1["nx"], ny=C1["ny"], dt=C1["dt"], Re=C1["Re"])
+    base = torch.from_numpy(inputs.wake_like_field(C1["ny"], C1["nx"], seed=0)).to(dev)
+    v0 = torch.from_numpy(inputs.gaussian_field(C1["ny"], C1["nx"], seed=1)).to(dev)
+    st.arnoldi_eigs(base, v0, m=C1["m"], nev=C1["nev"], tol=1e-3, T=C1["T"], max_restarts=0)   # warm graphs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e = st.arnoldi_eigs(base, v0, m=C1["m"], nev=C1["nev"], tol=C1["tol"], T=C1["T"], max_restarts=6)
+    torch.cuda.synchronize()
+    return {"seconds": time.perf_counter() - t0, "n_matvec": e.n_matvec, "n_conv": e.n_conv,
+            "mu": [[float(m.real), float(m.imag)] for m in e.mu], "precision": "f64"}
 
 
 def wake_stability_leg(args, dev):
@@ -707,10 +887,12 @@ def unet_train_leg(args, dev):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / n
     fl = learned_guess.train_step_flops(learned_guess.FEATURES, width, ny, nx, B)
-    fp32 = N_SMS * 128 * 2 * 2.07e9 / 1e12   # FP32 FMA peak at the maximum SM clock
+    bf16 = peaks().get("bf16_tflops")
+    tf = fl / (ms * 1e-3) / 1e12
     return {"grid": [nx, ny], "batch": B, "width": width, "params": net.count, "ms_per_train_step": ms,
-            "flops_per_step": fl, "tflops": fl / (ms * 1e-3) / 1e12, "fp32_fma_peak_tflops": fp32,
-            "frac_of_fp32_peak": fl / (ms * 1e-3) / 1e12 / fp32,
+            "flops_per_step": fl, "tflops": tf, "bf16_peak_tflops": bf16,
+            "frac_of_bf16_peak": tf / bf16 if bf16 else None,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM, burst)",
             "kernels": ("3x3 convolutions (forward, input and weight gradients) as implicit GEMMs on the tensor cores: "
                         "BF16 mma.sync, FP32 accumulation, FP32 gradients split bf16 hi + lo")}
 
@@ -782,6 +964,14 @@ def run_profile_case(args):
 
 def main():
     args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        import socket
+
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        cmd = replica_command(sys.argv[1:], args.gpus, port)
+        os.execv(cmd[0], cmd)
     if args.profile_case:
         run_profile_case(args)
         return
