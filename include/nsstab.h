@@ -381,6 +381,23 @@ int serve_eigs(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, 
                double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
                nsstab_eig_result* results, int* ngroups);
 
+/* The same batch of solves (FP32 stepper only: cfg->precision must be 32)
+ * with every grid advanced by one persistent launch per step kernel instead
+ * of one batched stepper per grid on its own stream.  Solves that share
+ * (nx, ny, dt) form a group as in serve_eigs; groups are admitted by device
+ * memory in waves (largest grids first, while the estimated footprint fits
+ * mem_budget, at most 8 grids a wave), and all solves of a wave run in
+ * lockstep Krylov-Schur rounds of Sec. 3.2.2: each round one product with M
+ * for every unfinished solve, made of T/dt_g steps of its own grid g, all
+ * grids stepped by the same launches (a grid sits out the steps beyond its
+ * own T/dt), captured once as a CUDA graph; then one batched CGS2 over all
+ * solves (vectors of different lengths).  Arguments, results and status as
+ * serve_eigs; results[i].group is the wave index and *nwaves (if not NULL)
+ * the number of waves.  Synchronous. */
+int serve_eigs_persistent(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+                          double tol, int max_restarts, double T, long long mem_budget,
+                          nsstab_eig_result* results, int* nwaves);
+
 /* ------------------------------------------------------------------------
  * Learned initial guess for the base-flow solve.
  *

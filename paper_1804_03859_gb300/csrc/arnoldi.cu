@@ -16,6 +16,7 @@
 // projected matrices are factorised on the host in FP64 (dense_eig.cpp).
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <cmath>
 #include <numeric>
 #include <vector>
@@ -92,12 +93,26 @@ double steady_seconds() {
 
 int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
                       double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs) {
-    const double delta = 0.05;   // wanted set |mu| >= 1 - delta (Sec. 3.2.2)
     const int nb = st->members();
+    std::vector<long> nm(nb, n);
+    auto prod = [&](const double* const* in, double* const* out) { return st->step_linear_ptrs(in, out, nsteps); };
+    return arnoldi_members_run(prod, nb, nm.data(), stream, v0, m, nev, tol, max_restarts, outs);
+}
+
+int arnoldi_members_run(const std::function<int(const double* const*, double* const*)>& prod, int nb,
+                        const long* nm, cudaStream_t stream, const double* const* v0, int m, int nev, double tol,
+                        int max_restarts, std::vector<ArnoldiOut>& outs) {
+    const double delta = 0.05;   // wanted set |mu| >= 1 - delta (Sec. 3.2.2)
     outs.resize(nb);
     const int ldb = m + 1;
+    long nmax = 0;
+    std::vector<size_t> off(nb + 1, 0);   // member b's basis at Vall + off[b]
+    for (int b = 0; b < nb; ++b) {
+        nmax = std::max(nmax, nm[b]);
+        off[b + 1] = off[b] + (size_t)nm[b] * (m + 1);
+    }
     DevBuf Vall, tmp, Cd;
-    NS_CUDA(cudaMalloc(&Vall.p, (size_t)nb * n * (m + 1) * sizeof(double)));
+    NS_CUDA(cudaMalloc(&Vall.p, off[nb] * sizeof(double)));
     NS_CUDA(cudaMalloc(&Cd.p, (size_t)(m + 1) * (m + 1) * sizeof(double)));
     GsBatch gs;
     struct Release {
@@ -113,13 +128,14 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
         std::vector<int> j0(nb, 0);
         std::vector<double> h(1), beta(nb), inv(nb);
         for (int b = 0; b < nb; ++b) {
-            mem[b].V = Vall.p + (size_t)b * n * (m + 1);
+            mem[b].V = Vall.p + off[b];
             mem[b].B.assign((size_t)ldb * m, 0.0);
-            NS_CUDA(cudaMemcpyAsync(mem[b].V, v0[b], n * sizeof(double), cudaMemcpyDeviceToDevice, stream));
+            NS_CUDA(cudaMemcpyAsync(mem[b].V, v0[b], nm[b] * sizeof(double), cudaMemcpyDeviceToDevice, stream));
             V0[b] = mem[b].V;
             W0[b] = mem[b].V;
         }
-        NS_TRY(cgs2_batch(nb, V0.data(), n, n, j0.data(), W0.data(), h.data(), 0, beta.data(), gs, stream));
+        NS_TRY(cgs2_batch(nb, V0.data(), nmax, nmax, j0.data(), W0.data(), h.data(), 0, beta.data(), gs, stream,
+                          nm));
         for (int b = 0; b < nb; ++b) {
             if (!(beta[b] > 0.0) || !std::isfinite(beta[b])) {
                 set_error("arnoldi_eigs: starting vector has zero or non-finite norm");
@@ -127,7 +143,7 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
             }
             inv[b] = 1.0 / beta[b];
         }
-        NS_TRY(scale_batch(nb, W0.data(), n, inv.data(), gs, stream));
+        NS_TRY(scale_batch(nb, W0.data(), nmax, inv.data(), gs, stream, nm));
     }
     std::vector<const double*> in(nb);
     std::vector<double*> out(nb), wv(nb);
@@ -147,16 +163,17 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
                 continue;
             }
             ++active;
-            in[b] = M.V + (size_t)M.j * n;
-            out[b] = M.V + (size_t)(M.j + 1) * n;
+            in[b] = M.V + (size_t)M.j * nm[b];
+            out[b] = M.V + (size_t)(M.j + 1) * nm[b];
             wv[b] = out[b];
             Vp[b] = M.V;
             jv[b] = M.j + 1;
         }
         if (active == 0) break;
         // one batched product with M, one batched CGS2
-        NS_TRY(st->step_linear_ptrs(in.data(), out.data(), nsteps));
-        NS_TRY(cgs2_batch(nb, Vp.data(), n, n, jv.data(), wv.data(), H.data(), m + 1, beta.data(), gs, stream));
+        NS_TRY(prod(in.data(), out.data()));
+        NS_TRY(cgs2_batch(nb, Vp.data(), nmax, nmax, jv.data(), wv.data(), H.data(), m + 1, beta.data(), gs, stream,
+                          nm));
         std::fill(inv.begin(), inv.end(), 0.0);
         std::vector<double*> scale_ptr(nb, nullptr);
         for (int b = 0; b < nb; ++b) {
@@ -182,7 +199,7 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
                 scale_ptr[b] = out[b];
             }
         }
-        NS_TRY(scale_batch(nb, scale_ptr.data(), n, inv.data(), gs, stream));
+        NS_TRY(scale_batch(nb, scale_ptr.data(), nmax, inv.data(), gs, stream, nm));
         // members with a full factorisation: Ritz pairs, convergence, restart
         for (int b = 0; b < nb; ++b) {
             Member& M = mem[b];
@@ -243,7 +260,8 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
             }
             p = psel;
             // V_p <- V_mm Z(:, :p), v_{p+1} <- v_{mm+1}
-            if (!tmp.p) NS_CUDA(cudaMalloc(&tmp.p, (size_t)n * m * sizeof(double)));
+            const long n = nm[b];
+            if (!tmp.p) NS_CUDA(cudaMalloc(&tmp.p, (size_t)nmax * m * sizeof(double)));
             NS_CUDA(cudaMemcpyAsync(Cd.p, M.Zm.data(), (size_t)mm * p * sizeof(double), cudaMemcpyHostToDevice,
                                     stream));
             NS_TRY(basis_combine(M.V, n, n, mm, Cd.p, p, tmp.p, n, stream));
@@ -293,7 +311,7 @@ int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double
                 }
             }
             NS_CUDA(cudaMemcpyAsync(Cd.p, Y.data(), Y.size() * sizeof(double), cudaMemcpyHostToDevice, stream));
-            NS_TRY(basis_combine(M.V, n, n, mm, Cd.p, M.k, o.eigvecs, n, stream));
+            NS_TRY(basis_combine(M.V, nm[b], nm[b], mm, Cd.p, M.k, o.eigvecs, nm[b], stream));
             NS_CUDA(cudaStreamSynchronize(stream));
         }
     }

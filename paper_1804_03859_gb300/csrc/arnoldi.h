@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <functional>
 #include <vector>
 
 #include "stepper.cuh"
@@ -26,6 +27,14 @@ double steady_seconds();
 // outs[b].eigvecs before the call to get Ritz vectors).
 int arnoldi_batch_run(StepperBase* st, cudaStream_t stream, long n, const double* const* v0, int m, int nev,
                       double tol, int max_restarts, int nsteps, std::vector<ArnoldiOut>& outs);
+
+// The same driver over nb members of possibly different lengths nm[b]
+// (device vectors on `stream`): prod(in, out) applies each member's M to
+// in[b] into out[b] for every non-null in[b] (null: the member is finished
+// and is skipped).
+int arnoldi_members_run(const std::function<int(const double* const*, double* const*)>& prod, int nb,
+                        const long* nm, cudaStream_t stream, const double* const* v0, int m, int nev, double tol,
+                        int max_restarts, std::vector<ArnoldiOut>& outs);
 
 // Block Krylov-Schur: one eigenproblem per parameter set of the stepper,
 // each with a block of b = members / sets vectors per product with M (the b

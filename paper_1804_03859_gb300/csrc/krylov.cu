@@ -137,10 +137,12 @@ __global__ void k_combine(const double* __restrict__ V, long ldv, long n, int m,
 // alone in the products (the norm pass uses its own count array).
 
 __global__ void k_gs_dot_b(const double* const* __restrict__ Vs, long ldv, long n, const int* __restrict__ js,
-                           const double* const* __restrict__ ws, double* __restrict__ partial, int ldp) {
+                           const double* const* __restrict__ ws, double* __restrict__ partial, int ldp,
+                           const long* __restrict__ ns) {
     const int b = blockIdx.y;
     const int j = js[b];
     if (j <= 0) return;
+    if (ns) ldv = n = ns[b];   // members of different lengths: ldv = n per member
     const double* V = Vs[b];
     const double* w = ws[b];
     double* part = partial + (size_t)b * gridDim.x * ldp;
@@ -177,10 +179,12 @@ __global__ void k_gs_dot_b(const double* const* __restrict__ Vs, long ldv, long 
 }
 
 __global__ void k_gs_update_b(double* const* __restrict__ ws, const double* const* __restrict__ Vs, long ldv, long n,
-                              const int* __restrict__ js, const double* __restrict__ h, int ldp) {
+                              const int* __restrict__ js, const double* __restrict__ h, int ldp,
+                              const long* __restrict__ ns) {
     const int b = blockIdx.y;
     const int j = js[b];
     if (j <= 0) return;
+    if (ns) ldv = n = ns[b];
     extern __shared__ double hs[];
     for (int c = threadIdx.x; c < j; c += blockDim.x) hs[c] = h[(size_t)b * ldp + c];
     __syncthreads();
@@ -193,9 +197,11 @@ __global__ void k_gs_update_b(double* const* __restrict__ ws, const double* cons
     }
 }
 
-__global__ void k_scale_b(double* const* __restrict__ ws, long n, const double* __restrict__ s) {
+__global__ void k_scale_b(double* const* __restrict__ ws, long n, const double* __restrict__ s,
+                          const long* __restrict__ ns) {
     double* w = ws[blockIdx.y];
     if (!w) return;
+    if (ns) n = ns[blockIdx.y];
     const double f = s[blockIdx.y];
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) w[i] *= f;
 }
@@ -369,6 +375,7 @@ int GsBatch::alloc(int nmem, int cols) {
     NS_CUDA(cudaMalloc(&jdev, (size_t)B * 2 * sizeof(int)));
     NS_CUDA(cudaMalloc(&ptrs, (size_t)B * 2 * sizeof(double*)));
     NS_CUDA(cudaMalloc(&sdev, (size_t)B * sizeof(double)));
+    NS_CUDA(cudaMalloc(&ndev, (size_t)B * sizeof(long)));
     NS_CUDA(cudaMallocHost(&hhost, ph * sizeof(double)));
     return NSSTAB_OK;
 }
@@ -379,8 +386,10 @@ void GsBatch::release() {
     if (jdev) cudaFree(jdev);
     if (ptrs) cudaFree(ptrs);
     if (sdev) cudaFree(sdev);
+    if (ndev) cudaFree(ndev);
     if (hhost) cudaFreeHost(hhost);
     partial = hdev = sdev = hhost = nullptr;
+    ndev = nullptr;
     jdev = nullptr;
     ptrs = nullptr;
     B = max_cols = 0;
@@ -390,10 +399,16 @@ void GsBatch::release() {
 // j[b] >= 0 (j[b] = 0: norm only; j[b] < 0: member skipped); h[b][0..j[b])
 // and beta[b] = ||w[b]|| to the host.  One synchronisation.
 int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j, double* const* w,
-               double* h /*host [nmem][ldh]*/, int ldh, double* beta, GsBatch& ws, cudaStream_t stream) {
+               double* h /*host [nmem][ldh]*/, int ldh, double* beta, GsBatch& ws, cudaStream_t stream,
+               const long* nm) {
     int jmax = 1;
     for (int b = 0; b < nmem; ++b) jmax = std::max(jmax, j[b]);
     NS_TRY(ws.alloc(nmem, jmax));
+    const long* nd = nullptr;
+    if (nm) {
+        NS_CUDA(cudaMemcpyAsync(ws.ndev, nm, nmem * sizeof(long), cudaMemcpyHostToDevice, stream));
+        nd = ws.ndev;
+    }
     const int ldp = ws.max_cols;
     std::vector<int> jh(2 * (size_t)nmem);
     std::vector<const double*> ph(2 * (size_t)nmem);
@@ -415,14 +430,14 @@ int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j,
     const dim3 g(ws.grid, nmem);
     const size_t sm = (size_t)jmax * sizeof(double);
     const dim3 gr((jmax + 31) / 32, nmem);
-    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp);
+    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp, nd);
     k_gs_reduce_par<<<gr, 256, 0, stream>>>(ws.partial, ws.grid, ldp, 0, jd, h1, ldp);
-    k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h1, ldp);
-    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp);
+    k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h1, ldp, nd);
+    k_gs_dot_b<<<g, kGsThreads, 0, stream>>>(Vd, ldv, n, jd, (const double* const*)wd, ws.partial, ldp, nd);
     k_gs_reduce_par<<<gr, 256, 0, stream>>>(ws.partial, ws.grid, ldp, 0, jd, h2, ldp);
-    k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h2, ldp);
+    k_gs_update_b<<<dim3(2 * ws.grid, nmem), kGsThreads, sm, stream>>>(wd, Vd, ldv, n, jd, h2, ldp, nd);
     k_gs_dot_b<<<g, kGsThreads, 0, stream>>>((const double* const*)wd, n, n, one, (const double* const*)wd,
-                                             ws.partial, ldp);
+                                             ws.partial, ldp, nd);
     k_gs_reduce_par<<<dim3(1, nmem), 256, 0, stream>>>(ws.partial, ws.grid, ldp, 0, one, b2, ldp);
     NS_LAUNCH_CHECK();
     NS_CUDA(cudaMemcpyAsync(ws.hhost, ws.hdev, (size_t)3 * nmem * ldp * sizeof(double), cudaMemcpyDeviceToHost,
@@ -438,13 +453,19 @@ int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j,
 }
 
 // w[b] *= s[b] for members with a non-null w[b]
-int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream) {
+int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream,
+                const long* nm) {
     NS_TRY(ws.alloc(nmem, 1));
+    const long* nd = nullptr;
+    if (nm) {
+        NS_CUDA(cudaMemcpyAsync(ws.ndev, nm, nmem * sizeof(long), cudaMemcpyHostToDevice, stream));
+        nd = ws.ndev;
+    }
     std::vector<double*> ph(w, w + nmem);
     NS_CUDA(cudaMemcpyAsync(ws.ptrs, ph.data(), nmem * sizeof(double*), cudaMemcpyHostToDevice, stream));
     std::vector<double> sh(s, s + nmem);
     NS_CUDA(cudaMemcpyAsync(ws.sdev, sh.data(), nmem * sizeof(double), cudaMemcpyHostToDevice, stream));
-    k_scale_b<<<dim3(ws.grid, nmem), kGsThreads, 0, stream>>>(ws.ptrs, n, ws.sdev);
+    k_scale_b<<<dim3(ws.grid, nmem), kGsThreads, 0, stream>>>(ws.ptrs, n, ws.sdev, nd);
     NS_LAUNCH_CHECK();
     return NSSTAB_OK;
 }

@@ -144,23 +144,26 @@ extern "C" int serve_eigs(const nsstab_config* cfg, int njobs, const nsstab_eig_
     }
 }
 
-static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
-                           double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
-                           nsstab_eig_result* results, int* ngroups) {
-    auto bad = [](const std::string& msg) {
-        set_error(msg);
+// Checks every job, groups the jobs by (nx, ny, dt) (in order of first
+// appearance; groups that do not fit the budget alone are split, and jobs
+// that cannot fit at all are marked out of memory), largest grids first.
+static int plan_units(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev, double tol,
+                      int max_restarts, double T, long long mem_budget, nsstab_eig_result* results,
+                      std::vector<int>& nsteps, std::vector<Unit>& units, size_t& budget, const char* who) {
+    auto bad = [&](const std::string& msg) {
+        set_error(std::string(who) + ": " + msg);
         return NSSTAB_ERR_INVALID_ARG;
     };
-    if (!cfg || !jobs || !results) return bad("serve_eigs: null argument");
-    if (njobs < 1) return bad("serve_eigs: need njobs >= 1");
-    if (m < 2 || m > 1024) return bad("serve_eigs: need 2 <= m <= 1024");
+    if (!cfg || !jobs || !results) return bad("null argument");
+    if (njobs < 1) return bad("need njobs >= 1");
+    if (m < 2 || m > 1024) return bad("need 2 <= m <= 1024");
     if (nev < 1 || nev >= m || nev > NSSTAB_SERVE_MAX_EIG - 1)
-        return bad("serve_eigs: need 1 <= nev < m and nev <= NSSTAB_SERVE_MAX_EIG - 1");
-    if (max_restarts < 0 || !(tol >= 0) || !(T > 0)) return bad("serve_eigs: need max_restarts >= 0, tol >= 0, T > 0");
-    std::vector<int> nsteps(njobs);
+        return bad("need 1 <= nev < m and nev <= NSSTAB_SERVE_MAX_EIG - 1");
+    if (max_restarts < 0 || !(tol >= 0) || !(T > 0)) return bad("need max_restarts >= 0, tol >= 0, T > 0");
+    nsteps.assign(njobs, 0);
     for (int i = 0; i < njobs; ++i) {
         const nsstab_eig_job& j = jobs[i];
-        const std::string at = "serve_eigs: job " + std::to_string(i) + ": ";
+        const std::string at = "job " + std::to_string(i) + ": ";
         if (!j.base || !j.v0) return bad(at + "null base or v0");
         nsstab_config c = *cfg;
         c.nx = j.nx;
@@ -176,18 +179,12 @@ static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig
         nsteps[i] = (int)kk;
     }
     std::memset(results, 0, sizeof(nsstab_eig_result) * (size_t)njobs);
-    int dev = 0;
-    NS_CUDA(cudaGetDevice(&dev));
-    size_t budget = (size_t)std::max<long long>(mem_budget, 0);
+    budget = (size_t)std::max<long long>(mem_budget, 0);
     if (mem_budget <= 0) {
         size_t fr = 0, tot = 0;
         NS_CUDA(cudaMemGetInfo(&fr, &tot));
         budget = (size_t)(0.8 * (double)fr);
     }
-    const int workers_max = max_concurrent > 0 ? max_concurrent : 4;
-
-    // group by (nx, ny, dt) in order of first appearance, then split groups
-    // that do not fit the budget
     std::map<std::tuple<int, int, double>, std::vector<int>> groups;
     std::vector<std::tuple<int, int, double>> order;
     for (int i = 0; i < njobs; ++i) {
@@ -195,7 +192,6 @@ static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig
         if (!groups.count(key)) order.push_back(key);
         groups[key].push_back(i);
     }
-    std::vector<Unit> units;
     int status = NSSTAB_OK;
     for (const auto& key : order) {
         const std::vector<int>& g = groups[key];
@@ -204,7 +200,7 @@ static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig
         while (cap > 0 && unit_bytes(nx, ny, cfg->precision, cap, m) > budget) --cap;
         if (cap == 0) {
             for (int i : g) results[i].status = NSSTAB_ERR_OUT_OF_MEMORY;
-            set_error("serve_eigs: a single solve on a " + std::to_string(nx) + "x" + std::to_string(ny) +
+            set_error(std::string(who) + ": a single solve on a " + std::to_string(nx) + "x" + std::to_string(ny) +
                       " grid exceeds the memory budget");
             status = NSSTAB_ERR_OUT_OF_MEMORY;
             continue;
@@ -220,10 +216,24 @@ static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig
             units.push_back(u);
         }
     }
-    // largest grids (longest solves) first
     std::stable_sort(units.begin(), units.end(),
                      [](const Unit& a, const Unit& b) { return (long)a.nx * a.ny > (long)b.nx * b.ny; });
     for (size_t i = 0; i < units.size(); ++i) units[i].group = (int)i;
+    return status;
+}
+
+static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+                           double tol, int max_restarts, double T, long long mem_budget, int max_concurrent,
+                           nsstab_eig_result* results, int* ngroups) {
+    std::vector<int> nsteps;
+    std::vector<Unit> units;
+    size_t budget = 0;
+    int status = plan_units(cfg, njobs, jobs, m, nev, tol, max_restarts, T, mem_budget, results, nsteps, units,
+                            budget, "serve_eigs");
+    if (status == NSSTAB_ERR_INVALID_ARG || status == NSSTAB_ERR_CUDA) return status;
+    int dev = 0;
+    NS_CUDA(cudaGetDevice(&dev));
+    const int workers_max = max_concurrent > 0 ? max_concurrent : 4;
     if (ngroups) *ngroups = (int)units.size();
 
     Shared sh;
@@ -281,4 +291,136 @@ static int serve_eigs_impl(const nsstab_config* cfg, int njobs, const nsstab_eig
         if (s == NSSTAB_NOT_CONVERGED && status == NSSTAB_OK) status = s;
     }
     return status;
+}
+
+// ---------------------------------------------------------------- persistent
+
+namespace nsstab {
+
+// One wave of groups in one ragged stepper: every solve of the wave
+// advanced by the same persistent launches, eigenproblems in lockstep rounds.
+static int run_wave(const nsstab_config& base_cfg, const std::vector<const Unit*>& wave, const nsstab_eig_job* jobs,
+                    const std::vector<int>& nsteps, int m, int nev, double tol, int max_restarts, double t0,
+                    int wave_index, nsstab_eig_result* results) {
+    cudaStream_t s = nullptr;
+    NS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    RaggedBase* rg = make_ragged_f32(s);
+    std::vector<int> order;   // job index of each member
+    int rc = NSSTAB_OK;
+    for (const Unit* u : wave) {
+        if (rc != NSSTAB_OK) break;
+        const int k = (int)u->jobs.size();
+        nsstab_config c = base_cfg;
+        c.nx = u->nx;
+        c.ny = u->ny;
+        c.dt = u->dt;
+        c.precision = 32;
+        std::vector<double> Re(k), D(k);
+        std::vector<const double*> base(k);
+        for (int i = 0; i < k; ++i) {
+            const nsstab_eig_job& j = jobs[u->jobs[i]];
+            Re[i] = j.Re;
+            D[i] = j.cyl_D;
+            base[i] = j.base;
+            order.push_back(u->jobs[i]);
+        }
+        c.Re = Re[0];
+        c.cyl_D = D[0];
+        rc = rg->add_group(c, k, Re.data(), D.data(), nsteps[u->jobs[0]], base.data());
+    }
+    if (rc == NSSTAB_OK) rc = rg->finalize();
+    const int nb = (int)order.size();
+    std::vector<ArnoldiOut> outs(nb);
+    if (rc == NSSTAB_OK) {
+        std::vector<long> nm(nb);
+        std::vector<const double*> v0(nb);
+        for (int b = 0; b < nb; ++b) {
+            nm[b] = rg->n_of(b);
+            v0[b] = jobs[order[b]].v0;
+        }
+        auto prod = [&](const double* const* in, double* const* out) { return rg->product(in, out); };
+        rc = arnoldi_members_run(prod, nb, nm.data(), s, v0.data(), m, nev, tol, max_restarts, outs);
+    }
+    const double t_end = steady_seconds();
+    for (int b = 0; b < nb; ++b) {
+        nsstab_eig_result& r = results[order[b]];
+        r.group = wave_index;
+        if (rc < 0) {
+            r.status = rc;
+            r.latency_s = t_end - t0;
+            continue;
+        }
+        const ArnoldiOut& o = outs[b];
+        r.status = o.status;
+        r.n_eig = o.n_eig;
+        r.n_conv = o.n_conv;
+        r.n_matvec = o.n_matvec;
+        r.latency_s = (o.done_at > 0.0 ? o.done_at : t_end) - t0;
+        for (int e = 0; e < o.n_eig && e < NSSTAB_SERVE_MAX_EIG; ++e) {
+            r.eig_re[e] = o.mu[e].real();
+            r.eig_im[e] = o.mu[e].imag();
+            r.resid[e] = o.resid[e];
+        }
+    }
+    delete rg;   // synchronises the stream and frees the groups' memory
+    cudaStreamDestroy(s);
+    return rc;
+}
+
+}  // namespace nsstab
+
+static int serve_persistent_impl(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+                                 double tol, int max_restarts, double T, long long mem_budget,
+                                 nsstab_eig_result* results, int* nwaves) {
+    if (cfg && cfg->precision != 32) {
+        set_error("serve_eigs_persistent: the persistent launch runs the FP32 stepper (precision 32)");
+        return NSSTAB_ERR_INVALID_ARG;
+    }
+    std::vector<int> nsteps;
+    std::vector<Unit> units;
+    size_t budget = 0;
+    int status = plan_units(cfg, njobs, jobs, m, nev, tol, max_restarts, T, mem_budget, results, nsteps, units,
+                            budget, "serve_eigs_persistent");
+    if (status == NSSTAB_ERR_INVALID_ARG || status == NSSTAB_ERR_CUDA) return status;
+    // waves: groups in order (largest grids first) while their memory fits
+    // the budget, at most kRagMaxGroups grids per launch
+    const double t0 = steady_seconds();
+    size_t next = 0;
+    int waves = 0;
+    std::string first_error;
+    while (next < units.size()) {
+        std::vector<const Unit*> wave;
+        size_t used = 0;
+        while (next < units.size() && (int)wave.size() < kRagMaxGroups &&
+               (wave.empty() || used + units[next].bytes <= budget)) {
+            used += units[next].bytes;
+            wave.push_back(&units[next]);
+            ++next;
+        }
+        const int rc = run_wave(*cfg, wave, jobs, nsteps, m, nev, tol, max_restarts, t0, waves, results);
+        if (rc < 0 && first_error.empty()) first_error = last_error();
+        ++waves;
+    }
+    if (nwaves) *nwaves = waves;
+    if (!first_error.empty()) set_error(first_error);
+    for (int i = 0; i < njobs; ++i) {
+        const int s = results[i].status;
+        if (s < 0 && status >= 0) status = s;
+        if (s == NSSTAB_NOT_CONVERGED && status == NSSTAB_OK) status = s;
+    }
+    return status;
+}
+
+extern "C" int serve_eigs_persistent(const nsstab_config* cfg, int njobs, const nsstab_eig_job* jobs, int m, int nev,
+                                     double tol, int max_restarts, double T, long long mem_budget,
+                                     nsstab_eig_result* results, int* nwaves) {
+    try {
+        return serve_persistent_impl(cfg, njobs, jobs, m, nev, tol, max_restarts, T, mem_budget, results, nwaves);
+    } catch (const std::exception& e) {
+        set_error(std::string("serve_eigs_persistent: ") + e.what());
+        return NSSTAB_ERR_OUT_OF_MEMORY;
+    } catch (...) {
+        set_error("serve_eigs_persistent: unexpected host exception");
+        return NSSTAB_ERR_CUDA;
+    }
 }

@@ -48,6 +48,26 @@ struct StepperBase {
     virtual int fused_rows() const = 0;
 };
 
+// Independent solves on grids of different sizes, advanced together by one
+// persistent launch per step kernel (FP32; ragged.cuh).  add_group adds k
+// solves on one grid (nsteps = T/dt steps per product with M) with their
+// base flows; finalize fixes the launch plans and captures a product round;
+// product applies every member's M (members numbered group by group; a null
+// in[m] skips member m).
+struct RaggedBase {
+    virtual ~RaggedBase() {}
+    virtual int add_group(const nsstab_config& cfg, int k, const double* Re, const double* D, int nsteps,
+                          const double* const* bases) = 0;
+    virtual int finalize() = 0;
+    virtual int members() const = 0;
+    virtual int groups() const = 0;
+    virtual long n_of(int m) const = 0;
+    virtual int product(const double* const* in, double* const* out) = 0;
+    virtual int launches_per_round() const = 0;
+};
+RaggedBase* make_ragged_f32(cudaStream_t stream);
+constexpr int kRagMaxGroups = 8;   // grids per ragged launch
+
 constexpr int kNumStepKernels = 6;   // col_poisson, row_inverse(psi), row_forward(rhs),
                                      // col_update, row_inverse(omega*, psi*), row_forward(pen)
 StepperBase* make_stepper(const nsstab_config& cfg, int nsets, const double* Re, const double* D, int per_set,
@@ -74,14 +94,18 @@ struct GsBatch {
     double* hhost = nullptr;     // pinned copy of hdev
     double* sdev = nullptr;      // [B] scale factors
     int* jdev = nullptr;         // [2][B] column counts
+    long* ndev = nullptr;        // [B] member lengths (members of different grids)
     double** ptrs = nullptr;     // [2][B] member pointers
     int B = 0, max_cols = 0, grid = 0;
     int alloc(int nmem, int cols);
     void release();
 };
+// nm (host, optional): per-member lengths, each also its basis's leading
+// dimension, in place of n and ldv (members on grids of different sizes).
 int cgs2_batch(int nmem, const double* const* V, long ldv, long n, const int* j, double* const* w,
-               double* h, int ldh, double* beta, GsBatch& ws, cudaStream_t stream);
-int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream);
+               double* h, int ldh, double* beta, GsBatch& ws, cudaStream_t stream, const long* nm = nullptr);
+int scale_batch(int nmem, double* const* w, long n, const double* s, GsBatch& ws, cudaStream_t stream,
+                const long* nm = nullptr);
 // Blocked Gram-Schmidt (two passes) of the b <= kMaxGsBlock columns of W[s]
 // (ldw apart) against the first J[s] columns of V[s], for every set with
 // J[s] > 0: H = V^T W, W -= V H, twice, each a single read of V for all b

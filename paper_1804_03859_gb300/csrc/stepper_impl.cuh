@@ -88,11 +88,10 @@ template <class T> struct Fields {
     const Cx<T>* twx[4]; const Cx<T>* twy[4];   // per-pass twiddle tables for LE = 1, 2, 3
 };
 
-// Offset the member-dependent pointers to member blockIdx.y (and its
-// parameter set).  Returns false for an inactive member: its blocks return
+// Offset the member-dependent pointers to member m (and its parameter
+// set).  Returns false for an inactive member: its blocks return
 // at once, so independent solves of a batch can drop out or idle.
-template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
-    const int m = blockIdx.y;
+template <class T> __device__ __forceinline__ bool member_view_at(Fields<T>& f, int m) {
     if (f.active && !f.active[m]) return false;
     const int set = m / f.bper;
     const size_t fo = (size_t)m * f.fs, co = (size_t)m * f.cs, so = (size_t)set * f.fs, to = (size_t)set * f.ts;
@@ -122,6 +121,8 @@ template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) {
     f.tB += to;
     return true;
 }
+
+template <class T> __device__ __forceinline__ bool member_view(Fields<T>& f) { return member_view_at(f, blockIdx.y); }
 
 // Diagonal operators at (kx, ky), kx in [0, nx/2]: Crank-Nicolson A = a/b
 // (FP32 steppers: A - 1), B = dt/b (both times the 1/(nx ny) of the inverse
@@ -226,13 +227,13 @@ __device__ __forceinline__ T row_value(const Fields<T>& f, int i, int j, bool sf
 #define NS_FFT_BOUNDS __launch_bounds__(LE == 3 ? 512 : 1024)
 
 template <class T, int MODE, int LE>
-__global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
+__device__ __forceinline__ void row_forward_body(const Fields<T>& f, int bx, int RP, int logRP, bool sfd,
+                                                 bool do_fft) {
     using C = Cx<T>;
-    if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int nx = f.nx, S = seq_stride(nx, RP, (int)sizeof(C) / 4);
-    const int pair0 = blockIdx.x * RP;
+    const int pair0 = bx * RP;
     constexpr int E = 1 << LE;   // RP*nx values over RP*nx/E threads: exactly E each
     constexpr bool PEN = (MODE == FWD_PEN_NL || MODE == FWD_PEN_LIN);
     T va[E], vb[E], ya[PEN ? E : 1], yb[PEN ? E : 1];
@@ -286,6 +287,12 @@ __global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool
     }
 }
 
+template <class T, int MODE, int LE>
+__global__ void NS_FFT_BOUNDS k_row_forward(Fields<T> f, int RP, int logRP, bool sfd, bool do_fft) {
+    if (!member_view(f)) return;
+    row_forward_body<T, MODE, LE>(f, blockIdx.x, RP, logRP, sfd, do_fft);
+}
+
 // What an inverse row pass transforms.  Each complex transform carries two
 // real rows: either rows (2p, 2p+1) of one array (a "same" pass) or row p of
 // two arrays.
@@ -298,10 +305,9 @@ enum InvIO {
 
 // Inverse x-transform of RP sequences per block, as selected by IO.
 template <class T, int LE, int IO>
-__global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP) {
+__device__ __forceinline__ void row_inverse_body(const Fields<T>& f, int bx, int RP, int logRP) {
     using C = Cx<T>;
-    if (!member_view(f)) return;
-    int pair0 = blockIdx.x * RP;
+    int pair0 = bx * RP;
     bool same = (IO == INV_PSI);
     const C* XA = (IO == INV_PSI || IO == INV_UV) ? f.X2 : f.X1;
     const C* XB = (IO == INV_UV) ? f.X3 : f.X2;
@@ -359,6 +365,12 @@ __global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP) {
     }
 }
 
+template <class T, int LE, int IO>
+__global__ void NS_FFT_BOUNDS k_row_inverse(Fields<T> f, int RP, int logRP) {
+    if (!member_view(f)) return;
+    row_inverse_body<T, LE, IO>(f, blockIdx.x, RP, logRP);
+}
+
 // ----------------------------------------------------------- column kernels
 
 // Packed kx = 0 column: Z = FFT_y(X0 + i XN).  Applying real operators f0 to
@@ -377,15 +389,14 @@ __device__ __forceinline__ C apply_packed0(C z, C zm_conj, T f0, T fN) {
 // v is zero; sy is odd in ky and acts alike on both halves of the packed
 // column).
 template <class T, int LE, bool VEL>
-__global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
+__device__ __forceinline__ void col_poisson_body(const Fields<T>& f, int bx, int CP, T scale) {
     using C = Cx<T>;
-    if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s = reinterpret_cast<C*>(smem_raw);
     const int ny = f.ny, logy = f.logy;
     const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
     C* s2 = s + (size_t)CP * S;   // VEL: v^
-    const int c0 = blockIdx.x * CP;
+    const int c0 = bx * CP;
     constexpr int E = 1 << LE;   // E elements per thread in each FFT pass
     // CP*ny values over blockDim threads: E each, or E/2 when the block has
     // twice the threads of one transform round (both inverse columns at once)
@@ -446,6 +457,12 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
     }
 }
 
+template <class T, int LE, bool VEL>
+__global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
+    if (!member_view(f)) return;
+    col_poisson_body<T, LE, VEL>(f, blockIdx.x, CP, scale);
+}
+
 // Forward y-transform of N (x-spectra in XN: X1, or X4 after the fused FP32
 // row pass); AB2/AB1 + Crank-Nicolson update
 //   omega*^ = tA omega^ + tB (c1 N^n + c0 N^{n-1}),  psi*^ = tP omega*^
@@ -453,16 +470,15 @@ __global__ void NS_FFT_BOUNDS k_col_poisson(Fields<T> f, int CP, T scale) {
 // y-transforms of omega*^ -> X1 and psi*^ -> X2 (kVel: u*'^ -> X2 and
 // v*^ -> X3, as in k_col_poisson).
 template <class T, int LE>
-__global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
+__device__ __forceinline__ void col_update_body(const Fields<T>& f, int bx, int CP, T c1, T c0, bool first) {
     using C = Cx<T>;
-    if (!member_view(f)) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* s1 = reinterpret_cast<C*>(smem_raw);
     const int ny = f.ny, logy = f.logy;
     const int S = seq_stride(ny, (ny >> LE) < 32 ? 32 / (ny >> LE) : 1, (int)sizeof(C) / 4);
     C* s2 = s1 + (size_t)CP * S;   // omega^ in, psi*^ out
     C* s3 = s2 + (size_t)CP * S;   // N^{n-1} in
-    const int c0i = blockIdx.x * CP;
+    const int c0i = bx * CP;
     constexpr int E = 1 << LE;   // E elements per thread in each FFT pass
     // CP*ny values over blockDim threads: E each, or E/2 when the block has
     // twice the threads of one transform round (the inverse transforms of
@@ -565,6 +581,12 @@ __global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool
         f.X2[g] = s2[c * S + sw<T>(j)];
         if (kF32<T>) f.X3[g] = s3[c * S + sw<T>(j)];
     }
+}
+
+template <class T, int LE>
+__global__ void NS_FFT_BOUNDS k_col_update(Fields<T> f, int CP, T c1, T c0, bool first) {
+    if (!member_view(f)) return;
+    col_update_body<T, LE>(f, blockIdx.x, CP, c1, c0, first);
 }
 
 // ------------------------------------------------------- pointwise kernels
@@ -675,8 +697,12 @@ static const size_t kMaxSmem = 200 * 1024;
 #define K_COLPSI(le) k_col_poisson<T, le, false>
 #define K_COLU(le) k_col_update<T, le>
 
+class RaggedF32;
+
 template <class T>
 class StepperImpl : public StepperBase {
+    friend class RaggedF32;   // drives float steppers' data through the ragged launches
+
   public:
     using C = Cx<T>;
     StepperImpl(const nsstab_config& cfg, int nsets, const double* Re, const double* D, int per_set,

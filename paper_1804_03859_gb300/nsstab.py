@@ -103,6 +103,9 @@ SIGNATURES = [
     ("block_arnoldi_eigs", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, _dp, _dp,
                                           _dp, ctypes.c_void_p, _ip, _ip, _ip]),
+    ("serve_eigs_persistent", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(EigJob),
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_longlong, ctypes.POINTER(EigJobResult), _ip]),
     ("serve_eigs", ctypes.c_int, [ctypes.POINTER(Config), ctypes.c_int, ctypes.POINTER(EigJob), ctypes.c_int,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                   ctypes.c_int, ctypes.POINTER(EigJobResult), _ip]),
@@ -282,14 +285,17 @@ def dense_schur_ordered(A: np.ndarray, thr: float):
 
 
 def serve_eigs(jobs, m: int, nev: int, tol: float, T: float, max_restarts: int = 0, mem_budget: int = 0,
-               max_concurrent: int = 0, **cfg):
-    """Many eigen-solves on mixed grids (C ``serve_eigs``).
+               max_concurrent: int = 0, persistent: bool = False, **cfg):
+    """Many eigen-solves on mixed grids (C ``serve_eigs``, or with
+    ``persistent=True`` C ``serve_eigs_persistent``: every grid advanced by
+    one persistent launch per step kernel, FP32 only).
 
     ``jobs``: list of dicts with keys nx, ny, dt, Re, cyl_D, base, v0 (base
     and v0 device tensors of shape [ny, nx]).  ``cfg``: shared physical
     parameters of ``nsstab_config``.  Returns (status, results, ngroups),
     results a list of dicts (status, mu, residual, n_conv, n_matvec, group,
-    latency_s) in job order."""
+    latency_s) in job order; for the persistent form group is the wave and
+    ngroups the number of waves."""
     import torch
 
     lib = load_library()
@@ -302,10 +308,14 @@ def serve_eigs(jobs, m: int, nev: int, tol: float, T: float, max_restarts: int =
     ng = ctypes.c_int()
     c = _cfg_from(**cfg)
     torch.cuda.current_stream().synchronize()   # the call's own streams do not wait on torch's
-    rc = lib.serve_eigs(ctypes.byref(c), len(jobs), arr, int(m), int(nev), float(tol), int(max_restarts), float(T),
-                        int(mem_budget), int(max_concurrent), out, ctypes.byref(ng))
+    if persistent:
+        rc = lib.serve_eigs_persistent(ctypes.byref(c), len(jobs), arr, int(m), int(nev), float(tol),
+                                       int(max_restarts), float(T), int(mem_budget), out, ctypes.byref(ng))
+    else:
+        rc = lib.serve_eigs(ctypes.byref(c), len(jobs), arr, int(m), int(nev), float(tol), int(max_restarts),
+                            float(T), int(mem_budget), int(max_concurrent), out, ctypes.byref(ng))
     if rc < 0 and all(out[i].status == 0 and out[i].n_eig == 0 for i in range(len(jobs))):
-        _check(rc, "serve_eigs")
+        _check(rc, "serve_eigs_persistent" if persistent else "serve_eigs")
     res = []
     for r in out:
         k = r.n_eig

@@ -136,3 +136,66 @@ def test_concurrent_groups_on_four_grids_raise_no_error():
         assert rc >= 0, nsstab.load_library().nsstab_last_error()
         assert ngroups == 4
         assert all(r["status"] >= 0 and r["n_matvec"] > 0 for r in res)
+
+
+# ------------------------------------------------- one persistent launch
+
+RAG_SPECS = [(64, 32, 0.02, 50.0, 1.0), (128, 64, 0.01, 45.0, 0.9), (64, 32, 0.02, 70.0, 1.1),
+             (256, 128, 0.005, 60.0, 1.0), (128, 64, 0.01, 80.0, 1.2)]
+RT, RM, RNEV, RTOL = 0.4, 48, 4, 1e-6
+
+
+@pytest.fixture(scope="module")
+def rag_jobs():
+    out = []
+    for i, (nx, ny, dt, re, d) in enumerate(RAG_SPECS):
+        out.append(dict(nx=nx, ny=ny, dt=dt, Re=re, cyl_D=d,
+                        base=_dev(inputs.wake_like_field(ny, nx, seed=80 + i)),
+                        v0=_dev(inputs.gaussian_field(ny, nx, seed=90 + i))))
+    return out
+
+
+def test_persistent_launch_matches_per_grid_batches(rag_jobs):
+    """Three grids with three time steps (20, 40 and 80 steps per product)
+    advanced by the same launches: every solve's leading eigenvalues equal
+    those of the per-grid batched steppers (both FP32; 1e-5 relative)."""
+    rc0, ref, ng0 = nsstab.serve_eigs(rag_jobs, m=RM, nev=RNEV, tol=RTOL, T=RT, max_restarts=80, precision=32)
+    rc1, got, nwaves = nsstab.serve_eigs(rag_jobs, m=RM, nev=RNEV, tol=RTOL, T=RT, max_restarts=80, precision=32,
+                                         persistent=True)
+    assert rc0 == nsstab.OK and rc1 == nsstab.OK
+    assert ng0 == 3 and nwaves == 1
+    for a, b in zip(ref, got):
+        assert b["status"] == nsstab.OK and b["n_conv"] == len(b["mu"]) == len(a["mu"])
+        assert b["group"] == 0 and b["latency_s"] > 0
+        for x in b["mu"]:
+            assert np.min(np.abs(a["mu"] - x)) <= 1e-5 * abs(x)
+
+
+def test_persistent_launch_pinned_to_the_dense_propagator(rag_jobs):
+    """The 64x32 solve at Re 50 through the persistent launch (alongside a
+    128x64 one): its Ritz values are eigenvalues of the assembled M."""
+    j = rag_jobs[0]
+    cfg = ns2d.Config(nx=64, ny=32, dt=0.02, Re=50.0, cyl_D=1.0)
+    mu = np.linalg.eigvals(dense.assemble_M(ns2d.Base.from_omega(j["base"].cpu().numpy(), cfg), RT, cfg))
+    mu = mu[krylov.leading_order(mu)][:6]
+    rc, res, _ = nsstab.serve_eigs([j, rag_jobs[1]], m=RM, nev=RNEV, tol=RTOL, T=RT, max_restarts=80,
+                                   precision=32, persistent=True)
+    assert rc == nsstab.OK
+    for x in res[0]["mu"]:
+        assert np.min(np.abs(mu - x)) <= 1e-5 * abs(x)
+
+
+def test_persistent_waves_under_a_small_budget_give_the_same_values(rag_jobs):
+    rc0, ref, _ = nsstab.serve_eigs(rag_jobs, m=RM, nev=RNEV, tol=RTOL, T=RT, max_restarts=80, precision=32,
+                                    persistent=True)
+    rc1, got, nwaves = nsstab.serve_eigs(rag_jobs, m=RM, nev=RNEV, tol=RTOL, T=RT, max_restarts=80, precision=32,
+                                         persistent=True, mem_budget=100 << 20)
+    assert rc0 == nsstab.OK and rc1 == nsstab.OK and nwaves >= 2
+    for a, b in zip(ref, got):
+        for x in b["mu"]:
+            assert np.min(np.abs(a["mu"] - x)) <= 1e-5 * abs(x)
+
+
+def test_persistent_launch_needs_the_fp32_stepper(rag_jobs):
+    with pytest.raises(nsstab.NsstabError, match="precision 32"):
+        nsstab.serve_eigs(rag_jobs[:1], m=RM, nev=RNEV, tol=RTOL, T=RT, precision=64, persistent=True)
