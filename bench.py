@@ -73,6 +73,12 @@ def parse():
     ap.add_argument("--members", type=int, default=1, help="batch members of --profile-case")
     ap.add_argument("--profile-unet", action="store_true",
                     help="only run the U-Net training leg (3 + 20 steps; for ncu launch lists)")
+    ap.add_argument("--serve-c5", action="store_true",
+                    help="only the serving batch on the grids {256x128 ... 2048x1024}: per-grid concurrent "
+                         "batches and the persistent launch, p50/p99 for both (minutes)")
+    ap.add_argument("--c3-full", action="store_true",
+                    help="only the Reynolds sweep at 2048x1024: 16 block eigenproblems (b 8) against one plain "
+                         "FP64 solve (tens of minutes)")
     return ap.parse_args()
 
 
@@ -649,7 +655,7 @@ BB_SETS = 16
 
 
 def batched_block_leg(args, dev, rate_grid=(2048, 1024), rate_block=8, rate_steps=40, eig_grid=(256, 128),
-                      eig_block=2, eig_m=128, single_m=128, restarts=30):
+                      eig_block=2, eig_m=128, single_m=128, restarts=30, single_batched=True):
     """Block Krylov-Schur over a Reynolds sweep: 16 Reynolds numbers in
     40..100, each its own eigenproblem with a block of b vectors per product
     with M, FP32 stepper, all 16 b fields advanced by one launch per kernel.
@@ -722,26 +728,33 @@ def batched_block_leg(args, dev, rate_grid=(2048, 1024), rate_block=8, rate_step
                          "products_total": int(sum(r.n_matvec for r in rs))}
         ref = rs
         del stb
-        sts = nsstab.Stepper(Re=Res, precision=32, **kw)
-        if not args.no_tune:
-            sts.stepper_autotune(reps=3)
+        torch.cuda.empty_cache()
         v1 = v[::block].contiguous()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rs = sts.batch_arnoldi_eigs(bases, v1, m=single_m, nev=4, tol=TOL32, T=T_SAMPLE, max_restarts=restarts)
-        runs["single_vector_batched"] = {"seconds": time.perf_counter() - t0, "m": single_m,
-                                         "sets_converged": int(sum(r.n_conv >= len(r.mu) for r in rs)),
-                                         "products_total": int(sum(r.n_matvec for r in rs))}
-        agree = [float(max(np.min(np.abs(b.mu - x)) / abs(x) for x in a.mu)) for a, b in zip(ref, rs)
-                 if a.n_conv >= len(a.mu) and b.n_conv >= len(b.mu)]
-        del sts
+        agree = []
+        if single_batched:
+            sts = nsstab.Stepper(Re=Res, precision=32, **kw)
+            if not args.no_tune:
+                sts.stepper_autotune(reps=3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rs = sts.batch_arnoldi_eigs(bases, v1, m=single_m, nev=4, tol=TOL32, T=T_SAMPLE, max_restarts=restarts)
+            runs["single_vector_batched"] = {"seconds": time.perf_counter() - t0, "m": single_m,
+                                             "sets_converged": int(sum(r.n_conv >= len(r.mu) for r in rs)),
+                                             "products_total": int(sum(r.n_matvec for r in rs))}
+            agree = [float(max(np.min(np.abs(b.mu - x)) / abs(x) for x in a.mu)) for a, b in zip(ref, rs)
+                     if a.n_conv >= len(a.mu) and b.n_conv >= len(b.mu)]
+            del sts
         st64 = nsstab.Stepper(Re=Res[0], **kw)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r64 = st64.arnoldi_eigs(bases[0], v1[0], m=single_m, nev=4, tol=1e-8, T=T_SAMPLE, max_restarts=restarts)
         one = time.perf_counter() - t0
         runs["plain_fp64_sequential_estimate"] = {"seconds": 16 * one, "one_solve_seconds": one, "m": single_m,
-                                                  "tol": 1e-8, "converged": bool(r64.n_conv >= len(r64.mu))}
+                                                  "tol": 1e-8, "converged": bool(r64.n_conv >= len(r64.mu)),
+                                                  "n_matvec": r64.n_matvec}
+        if ref[0].n_conv >= len(ref[0].mu) and r64.n_conv >= len(r64.mu):
+            runs["set0_rel_diff_block_fp32_vs_plain_fp64"] = float(
+                max(np.min(np.abs(r64.mu - x)) / abs(x) for x in ref[0].mu))
         out["time_to_eigs"] = {"grid": [nx, ny], "nev": 4, "tol": TOL32, "T": T_SAMPLE, **runs,
                                "max_rel_diff_block_vs_single": max(agree) if agree else None}
     return out
@@ -901,13 +914,16 @@ SERVE_JOBS = 24
 SERVE_M, SERVE_NEV, SERVE_RESTARTS = 128, 4, 8
 
 
-def serve_leg(args, dev):
-    """Latency and throughput of serve_eigs on a seeded mixed-grid batch."""
+def serve_leg(args, dev, persistent=False, grids=None):
+    """Latency and throughput of serve_eigs on a seeded mixed-grid batch
+    (persistent: serve_eigs_persistent, every grid in one launch per step
+    kernel)."""
     import torch
 
     from paper_1804_03859_gb300 import inputs, nsstab
 
-    grids = [tuple(int(x) for x in g.lower().split("x")) for g in args.serve_grids.split(",")]
+    if grids is None:
+        grids = [tuple(int(x) for x in g.lower().split("x")) for g in args.serve_grids.split(",")]
     rng = np.random.default_rng(5)
     jobs = []
     for i in range(SERVE_JOBS):
@@ -919,7 +935,7 @@ def serve_leg(args, dev):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     rc, res, ngroups = nsstab.serve_eigs(jobs, m=SERVE_M, nev=SERVE_NEV, tol=TOL32, T=T_SAMPLE,
-                                         max_restarts=SERVE_RESTARTS, precision=32)
+                                         max_restarts=SERVE_RESTARTS, precision=32, persistent=persistent)
     wall = time.perf_counter() - t0
     lat = np.array([r["latency_s"] for r in res])
     pts = sum(r["n_matvec"] * j["nx"] * j["ny"] * round(T_SAMPLE / j["dt"]) for r, j in zip(res, jobs))
@@ -927,7 +943,8 @@ def serve_leg(args, dev):
     for j in jobs:
         k = f"{j['nx']}x{j['ny']}"
         mix[k] = mix.get(k, 0) + 1
-    return {"solves": SERVE_JOBS, "grids": mix, "Re": [40.0, 120.0], "cyl_D": [0.8, 1.2], "precision": "f32",
+    return {"form": "persistent launch over all grids" if persistent else "per-grid batches on concurrent streams",
+            "solves": SERVE_JOBS, "grids": mix, "Re": [40.0, 120.0], "cyl_D": [0.8, 1.2], "precision": "f32",
             "krylov_m": SERVE_M, "nev": SERVE_NEV, "max_restarts": SERVE_RESTARTS, "tol": TOL32, "T": T_SAMPLE,
             "groups": ngroups, "status": rc, "matvecs": int(sum(r["n_matvec"] for r in res)),
             "error": nsstab.load_library().nsstab_last_error().decode() if rc < 0 else None,
@@ -936,6 +953,41 @@ def serve_leg(args, dev):
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max()), "min": float(lat.min())},
             "grid_pt_steps_per_s": pts / wall}
+
+
+C5_GRIDS = [(256, 128), (512, 256), (1024, 512), (2048, 1024)]
+
+
+def run_serve_c5(args):
+    """Both serving forms on the same 24 solves drawn from the four grids."""
+    import torch
+
+    from paper_1804_03859_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda")
+    out = {"workload": "24 eigen-solves, grids from 256x128..2048x1024, Re U[40,120], D U[0.8,1.2], FP32, "
+                       f"m {SERVE_M}, nev {SERVE_NEV}, tol {TOL32}, T {T_SAMPLE}"}
+    out["concurrent_streams"] = serve_leg(args, dev, persistent=False, grids=C5_GRIDS)
+    torch.cuda.empty_cache()
+    out["persistent"] = serve_leg(args, dev, persistent=True, grids=C5_GRIDS)
+    print(json.dumps(out))
+
+
+def run_c3_full(args):
+    """The Reynolds sweep at its stated size: 16 Reynolds numbers in 40..100
+    at 2048x1024, each its own block eigenproblem (b 8, one synthetic wake
+    base per set), FP32 stepper, against one plain FP64 single-vector solve
+    at the same grid (times 16 for the sequential estimate)."""
+    import torch
+
+    from paper_1804_03859_gb300 import build
+
+    build.build()
+    dev = torch.device("cuda")
+    r = batched_block_leg(args, dev, rate_grid=None, eig_grid=(2048, 1024), eig_block=8, eig_m=256,
+                          single_m=128, restarts=40, single_batched=False)
+    print(json.dumps(r))
 
 
 def run_profile_case(args):
@@ -974,6 +1026,12 @@ def main():
         os.execv(cmd[0], cmd)
     if args.profile_case:
         run_profile_case(args)
+        return
+    if args.serve_c5:
+        run_serve_c5(args)
+        return
+    if args.c3_full:
+        run_c3_full(args)
         return
     if args.profile_unet:
         import torch
