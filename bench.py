@@ -986,7 +986,7 @@ def run_c3_full(args):
     build.build()
     dev = torch.device("cuda")
     r = batched_block_leg(args, dev, rate_grid=None, eig_grid=(2048, 1024), eig_block=8, eig_m=256,
-                          single_m=128, restarts=40, single_batched=False)
+                          single_m=128, restarts=8, single_batched=False)
     print(json.dumps(r))
 
 
