@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--serve-c5", action="store_true",
                     help="only the serving batch on the grids {256x128 ... 2048x1024}: per-grid concurrent "
                          "batches and the persistent launch, p50/p99 for both (minutes)")
+    ap.add_argument("--c1-sfd", action="store_true",
+                    help="only the 128x64 case's base flow by selective frequency damping to r <= 1e-10: the "
+                         "configured (chi 0.1, Delta 0.5), then Delta 2 and (chi 0.2, Delta 2), against Newton")
     ap.add_argument("--c3-full", action="store_true",
                     help="only the Reynolds sweep at 2048x1024: 16 block eigenproblems (b 8) against one plain "
                          "FP64 solve (tens of minutes)")
@@ -974,6 +977,39 @@ def run_serve_c5(args):
     print(json.dumps(out))
 
 
+def run_c1_sfd(args):
+    """Selective frequency damping (Eq. 40) on the 128x64 cylinder case at
+    Re 50 (dt 0.01) from rest to r <= 1e-10 with a step budget, with the
+    configured gains and with two others; every final state against the
+    Newton-Krylov base flow.  For the leading mode of this case (growth
+    0.066, frequency 0.81) the closed loop (s - lam + chi)(s + 1/Delta) =
+    chi/Delta has rates +0.051 (chi 0.1, Delta 0.5: unstable), -0.0038
+    (Delta 2) and -0.071 (chi 0.2, Delta 2)."""
+    import torch
+
+    from paper_1804_03859_gb300 import build, nsstab
+
+    build.build()
+    kw = dict(nx=128, ny=64, dt=0.01, Re=50.0)
+    st = nsstab.Stepper(**kw)
+    qn = torch.zeros(64, 128, dtype=torch.float64, device="cuda")
+    st.sfd_baseflow(qn, chi=0.1, Delta=0.5, tol=0.0, max_steps=300, check_every=300)
+    rcn, rn, itn, _ = st.newton_krylov_fixedpoint(qn, T=0.4, gmres_m=50, tol=1e-10, max_newton=30)
+    out = {"workload": "cylinder 128x64, Re 50, dt 0.01: SFD from rest to r <= 1e-10",
+           "newton": {"status": rcn, "residual": rn, "iters": itn}, "runs": []}
+    for chi, Delta, budget in ((0.1, 0.5, 400_000), (0.1, 2.0, 1_200_000), (0.2, 2.0, 400_000)):
+        q = torch.zeros(64, 128, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, r, steps = st.sfd_baseflow(q, chi=chi, Delta=Delta, tol=1e-10, max_steps=budget, check_every=2000)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        d = float(torch.max(torch.abs(q - qn)) / torch.max(torch.abs(qn))) if rcn == nsstab.OK else None
+        out["runs"].append({"chi": chi, "Delta": Delta, "step_budget": budget, "status": rc, "residual": r,
+                            "steps": steps, "seconds": el, "max_rel_diff_vs_newton": d})
+    print(json.dumps(out))
+
+
 def run_c3_full(args):
     """The Reynolds sweep at its stated size: 16 Reynolds numbers in 40..100
     at 2048x1024, each its own block eigenproblem (b 8, one synthetic wake
@@ -1032,6 +1068,9 @@ def main():
         return
     if args.c3_full:
         run_c3_full(args)
+        return
+    if args.c1_sfd:
+        run_c1_sfd(args)
         return
     if args.profile_unet:
         import torch

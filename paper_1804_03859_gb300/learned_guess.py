@@ -260,7 +260,91 @@ def run(args) -> dict:
                                             if r["learned"]["guess_rel_err"] is not None] or [np.nan])),
         "rows": out_rows,
         "total_seconds": time.perf_counter() - t_all,
+        "_net": net, "_scale": scale,
     }
+
+
+def spectral_resample(q: np.ndarray, ny: int, nx: int) -> np.ndarray:
+    """A periodic field [ny0][nx0] on a finer ny x nx grid of the same box by
+    zero-padding its Fourier spectrum (the Nyquist row and column of the
+    coarse grid split evenly between +k and -k), i.e. the band-limited
+    interpolant sampled on the finer grid."""
+    ny0, nx0 = q.shape
+    F = np.fft.fft2(q) * ((ny * nx) / (ny0 * nx0))
+
+    def maps(n0, n):
+        h = n0 // 2
+        src = np.r_[0:h, h, h, h + 1:n0]
+        dst = np.r_[0:h, h, n - h, n - h + 1:n]
+        w = np.ones(src.size)
+        w[h] = w[h + 1] = 0.5
+        return src, dst, w
+
+    sr, dr, wr = maps(ny0, ny)
+    sc, dc, wc = maps(nx0, nx)
+    G = np.zeros((ny, nx), dtype=complex)
+    R, Cc = np.meshgrid(dr, dc, indexing="ij")
+    np.add.at(G, (R, Cc), F[np.ix_(sr, sc)] * wr[:, None] * wc[None, :])   # +k and -k coincide when n = n0
+    return np.real(np.fft.ifft2(G))
+
+
+def run_c4(args, learned: dict) -> dict:
+    """The largest Newton case: 4096 x 2048, Re 100, D 1, T 1, GMRES(50), the
+    FP32 propagator of the equations linearised about the current iterate as
+    Jacobian, FP64 map and residual, r <= 1e-10; from the plain start (SFD
+    from rest, args.c4_sfd_steps steps) and from the network's prediction at
+    the training grid resampled spectrally to 4096 x 2048."""
+    import torch
+
+    nx, ny, Re, D = 4096, 2048, 100.0, 1.0
+    dt = 0.01 * 128 / nx
+    kw = dict(nx=nx, ny=ny, dt=dt, Re=Re, cyl_D=D)
+    out = {"workload": f"Newton-Krylov base flow {nx}x{ny}, Re {Re:g}, D {D:g}, T 1, GMRES(50), tol 1e-10",
+           "jacobian": "frozen (propagator of the linearised equations about the iterate), FP32"}
+
+    def solve(q, label):
+        st = nsstab.Stepper(**kw)
+        lin = nsstab.Stepper(precision=32, **kw)
+        _sync()
+        t0 = time.perf_counter()
+        rc, r, it, mv = st.newton_krylov_fixedpoint(q, T=1.0, gmres_m=50, tol=1e-10, max_newton=args.c4_max_newton,
+                                                    lin=lin, jacobian="frozen")
+        _sync()
+        out[label] = {"status": rc, "residual": r, "newton_iters": it, "jacobian_products": mv,
+                      "newton_seconds": time.perf_counter() - t0}
+        del st, lin
+        torch.cuda.empty_cache()
+
+    st = nsstab.Stepper(**kw)
+    q = torch.zeros(ny, nx, dtype=torch.float64, device="cuda")
+    _sync()
+    t0 = time.perf_counter()
+    st.sfd_baseflow(q, chi=args.chi, Delta=args.Delta, tol=0.0, max_steps=args.c4_sfd_steps,
+                    check_every=args.c4_sfd_steps)
+    _sync()
+    t_sfd = time.perf_counter() - t0
+    r0 = st.stepper_residual(q)
+    del st
+    solve(q, "plain")
+    out["plain"].update(start=f"SFD from rest, {args.c4_sfd_steps} steps (chi {args.chi:g}, Delta {args.Delta:g})",
+                        start_seconds=t_sfd, start_residual=r0)
+    net, scale = learned["_net"], learned["_scale"]
+    x = torch.from_numpy(features(args.nx, args.ny, Re, D)[None].astype(np.float32)).cuda()
+    y = torch.empty(1, args.ny, args.nx, dtype=torch.float32, device="cuda")
+    _sync()
+    t0 = time.perf_counter()
+    net.unet_forward(x, y)
+    g = (y[0].to(torch.float64) * scale).cpu().numpy()
+    q = torch.from_numpy(spectral_resample(g, ny, nx)).cuda()
+    _sync()
+    t_pred = time.perf_counter() - t0
+    st = nsstab.Stepper(**kw)
+    r1 = st.stepper_residual(q)
+    del st
+    solve(q, "learned")
+    out["learned"].update(start=f"U-Net prediction at {args.nx}x{args.ny}, resampled spectrally",
+                          start_seconds=t_pred, start_residual=r1)
+    return out
 
 
 def parse(argv=None):
@@ -285,6 +369,10 @@ def parse(argv=None):
     ap.add_argument("--chains", type=int, default=8, help="concurrent continuation runs for the labels")
     ap.add_argument("--re-min", dest="re_min", type=float, default=40.0)
     ap.add_argument("--re-max", dest="re_max", type=float, default=150.0)
+    ap.add_argument("--c4", action="store_true",
+                    help="after training, the 4096x2048 Re 100 Newton solve from the plain and the learned start")
+    ap.add_argument("--c4-sfd-steps", dest="c4_sfd_steps", type=int, default=400)
+    ap.add_argument("--c4-max-newton", dest="c4_max_newton", type=int, default=20)
     return ap.parse_args(argv)
 
 
@@ -292,7 +380,12 @@ def main(argv=None):
     from . import build
 
     build.build()
-    res = run(parse(argv))
+    args = parse(argv)
+    res = run(args)
+    if args.c4 and "_net" in res:
+        res["c4"] = run_c4(args, res)
+    res.pop("_net", None)
+    res.pop("_scale", None)
     print(json.dumps(res))
 
 

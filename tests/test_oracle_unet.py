@@ -101,3 +101,23 @@ def test_bf16_storage_changes_little(bf):
     y1, _ = unet.forward(theta, x, in_ch, width, bf16_storage=bf)
     rel = np.linalg.norm(y1 - y0) / np.linalg.norm(y0)
     assert (rel == 0.0) if not bf else (0.0 < rel < 5e-2)
+
+
+def test_spectral_resampling_of_the_learned_start_is_the_band_limited_interpolant():
+    """The learned Newton start is predicted on the training grid and
+    resampled to the solve grid: every other point of the resampled field is
+    the original field, and a band-limited mode is reproduced exactly."""
+    from paper_1804_03859_gb300.learned_guess import spectral_resample
+
+    rng = np.random.default_rng(3)
+    q = rng.standard_normal((16, 32))
+    f = spectral_resample(q, 64, 128)
+    assert np.allclose(f[::4, ::4], q, atol=1e-12)
+    assert np.allclose(spectral_resample(q, 16, 32), q, atol=1e-12)
+    y = np.arange(16)[:, None] / 16
+    x = np.arange(32)[None, :] / 32
+    g = np.cos(2 * np.pi * 3 * x) * np.sin(2 * np.pi * 2 * y) + 0.3 * np.cos(2 * np.pi * 8 * y)
+    Y = np.arange(64)[:, None] / 64
+    X = np.arange(128)[None, :] / 128
+    G = np.cos(2 * np.pi * 3 * X) * np.sin(2 * np.pi * 2 * Y) + 0.3 * np.cos(2 * np.pi * 8 * Y)
+    assert np.allclose(spectral_resample(g, 64, 128), G, atol=1e-12)
