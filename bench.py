@@ -71,6 +71,8 @@ def parse():
                     help="only run --steps linearised steps of one stepper on this grid (for ncu captures)")
     ap.add_argument("--precision", type=int, default=64, help="stepper precision of --profile-case (64, 48, 32)")
     ap.add_argument("--members", type=int, default=1, help="batch members of --profile-case")
+    ap.add_argument("--fused-rows", dest="fused_rows", type=int, default=0,
+                    help="--profile-case, FP32: fused row passes over strips of this many rows (0: six kernels)")
     ap.add_argument("--profile-unet", action="store_true",
                     help="only run the U-Net training leg (3 + 20 steps; for ncu launch lists)")
     ap.add_argument("--serve-c5", action="store_true",
@@ -1043,10 +1045,13 @@ def run_profile_case(args):
     base = torch.from_numpy(np.stack([inputs.wake_like_field(ny, nx, seed=k) for k in range(B)]).reshape(shape)).cuda()
     v = torch.from_numpy(np.stack([inputs.gaussian_field(ny, nx, seed=10 + k) for k in range(B)]).reshape(shape)).cuda()
     w = torch.empty_like(v)
+    if args.fused_rows:
+        st.stepper_set_fused_rows(args.fused_rows)
     st.stepper_set_base(base)
     st.apply_expTL(None, v, w, args.steps * dt)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": args.profile_case, "precision": args.precision, "members": B,
+                      "fused_rows": st.stepper_get_fused_rows() if args.precision == 32 else 0,
                       "steps": args.steps, "max_abs": float(w.abs().max())}))
 
 
