@@ -10,9 +10,14 @@
 // cycles, so each sub-partition needs its own warp).  The Stockham (self-sorting) index map is used, so input and
 // output are both in natural order and no bit reversal is needed.
 //
-// Shared-memory layout: sequence f occupies S = padded_len(N) (or more)
-// slots starting at s + f*S; element e sits at slot sw<T>(e) = e + e/8, which
-// keeps the stride-8 stores of the first pass free of bank conflicts.
+// Shared-memory layout: sequence f occupies S = seq_stride(...) >= N (FP32:
+// N + N/16) slots starting at s + f*S; element e sits at slot sw<T>(e),
+// which keeps the strided stores of the early passes free of bank
+// conflicts: FP64 and double-float XOR-swizzle within each 128-byte bank
+// row; FP32 inserts one pad slot after every 16 elements, so that slot(e +
+// 16 j) = slot(e) + 17 j and the reads of a pass (stride N/R) and the writes
+// of the passes with stride >= 16 are linear in r: one address per pass
+// instead of one per element.
 //
 // Twiddles come from precomputed per-pass tables (twiddle_table_len; built
 // on the host in extended precision) read through the read-only cache: on
@@ -41,22 +46,23 @@ namespace nsstab {
 // unit-stride accesses and the stride-8 stores of the first radix-8 pass
 // free of bank conflicts, without padding.
 template <class T> __device__ __forceinline__ int sw(int i);
-template <> __device__ __forceinline__ int sw<float>(int i) { return i ^ ((i >> 4) & 15); }
+template <> __device__ __forceinline__ int sw<float>(int i) { return i + (i >> 4); }
 template <> __device__ __forceinline__ int sw<double>(int i) { return i ^ ((i >> 3) & 7); }
 template <> __device__ __forceinline__ int sw<df64>(int i) { return i ^ ((i >> 3) & 7); }
-__host__ __device__ constexpr int padded_len(int n) { return n; }
+// Slots a sequence of n elements occupies (elem_words = element size / 4
+// bytes; 2 is FP32 complex, whose layout pads one slot per 16 elements).
+__host__ __device__ constexpr int padded_len(int n, int elem_words) { return elem_words == 2 ? n + (n >> 4) : n; }
 // Distance (in elements) between consecutive sequences in shared memory.
 // When `rp` sequences share one shared-memory wavefront (element-interleaved
 // staging loops, or short sequences several to a warp), their starts are
-// spread over the 32 four-byte banks, 32/rp banks apart.  elem_words =
-// element size / 4 bytes.
+// spread over the 32 four-byte banks, 32/rp banks apart.
 __host__ __device__ inline int seq_stride(int n, int rp, int elem_words) {
-    int s = n;
+    int s = padded_len(n, elem_words);
     if (rp <= 1) return s;
     const int target = (32 / rp) & 31;
     for (int i = 0; i < 32; ++i, ++s)
         if (((s * elem_words) & 31) == target) return s;
-    return n + 1;
+    return padded_len(n, elem_words) + 1;
 }
 
 // Twiddle tables, one per elements-per-thread choice LE: for every pass
@@ -170,27 +176,48 @@ template <bool INV, class T, int LE, int LR>
 __device__ __forceinline__ void stockham_pass(Cx<T>* d, int q, int lq, int logN, int nsl,
                                               const Cx<T>* __restrict__ tw, bool act) {
     constexpr int E = 1 << LE, R = 1 << LR, U = E / R;
+    constexpr bool PAD = std::is_same<T, float>::value;   // sw<float>: linear in steps of 16
     Cx<T> v[E];
     if (act) {
+        const int M = 1 << (logN - LR);   // read stride
+        if (PAD && M >= 16) {
+            const int Mp = M + (M >> 4);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
+                const Cx<T>* p = d + sw<T>(q + (u << lq));
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[u * R + r] = d[sw<T>(q + (u << lq) + (r << (logN - LR)))];
+                for (int r = 0; r < R; ++r) v[u * R + r] = p[r * Mp];
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[u * R + r] = d[sw<T>(q + (u << lq) + (r << (logN - LR)))];
+        }
     }
     __syncthreads();
     if (act) {
+        const int Ns = 1 << nsl;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int b = q + (u << lq);
-            const int k = b & ((1 << nsl) - 1);
+            const int k = b & (Ns - 1);
             if (nsl > 0) {
+                const Cx<T>* twk = tw + kTwWidth<T> * k;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[u * R + r] = twiddle<INV, T>(v[u * R + r], tw, (r << nsl) + k);
+                for (int r = 1; r < R; ++r) v[u * R + r] = twiddle<INV, T>(v[u * R + r], twk, r * Ns);
             }
             dft_r<INV, T, LR>(v + u * R);
             const int base = ((b - k) << LR) + k;
+            if (PAD && Ns >= 16) {
+                Cx<T>* p = d + sw<T>(base);
+                const int Np = Ns + (Ns >> 4);
 #pragma unroll
-            for (int r = 0; r < R; ++r) d[sw<T>(base + (r << nsl))] = v[u * R + r];
+                for (int r = 0; r < R; ++r) p[r * Np] = v[u * R + r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) d[sw<T>(base + r * Ns)] = v[u * R + r];
+            }
         }
     }
     __syncthreads();

@@ -37,13 +37,17 @@
 // rounds; the FP32 radix-8 pass with compensated twiddles needs about 100
 // registers, which 512 threads leave room for), the forward transform also
 // at 8 (fewer passes and one twiddle table for both directions).
-// Shared memory 96 G nx bytes (192 KB).
+// Shared memory 40 G (nx + nx/16) + 56 G nx bytes (197 KB).
 #pragma once
 
 namespace nsstab {
 
 constexpr int kRollThreads = 512;
 constexpr int kRollPoints = 2048;   // G * nx
+
+// Shared memory of a fused row pass over G strips of nx points (pts = G nx):
+// five padded sequences, the staged x-spectra and the per-row operands.
+inline size_t roll_smem(int pts) { return (size_t)40 * padded_len(pts, 2) + (size_t)56 * pts; }
 
 struct RollShape {
     int R;           // rows per strip (even, divides ny)
@@ -183,11 +187,12 @@ __global__ void __launch_bounds__(kRollThreads, 1) k_row_roll(Fields<float> f0, 
     constexpr bool AUX = RollArrays<MODE>::AUX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nx = f0.nx, nh = f0.nxh, ny = f0.ny, G = rs.G;
-    // [g][5][nx]: ring slots 0..2, M0, M1
+    const int nxp = padded_len(nx, 2);   // slots of one sequence (sw<float> pads)
+    // [g][5][nxp]: ring slots 0..2, M0, M1
     float2* seqs = reinterpret_cast<float2*>(smem_raw);
-    float4* stage = reinterpret_cast<float4*>(seqs + (size_t)G * 5 * nx);   // [g][3][nx/2]
-    float* aux = reinterpret_cast<float*>(stage + (size_t)G * 3 * nh);       // [g][8][nx]
-    auto seq = [=](int g, int slot) { return seqs + ((size_t)g * 5 + slot) * nx; };
+    float4* stage = reinterpret_cast<float4*>(seqs + (size_t)G * 5 * nxp);   // [g][3][nx/2]
+    float* aux = reinterpret_cast<float*>(stage + (size_t)G * 3 * nh);        // [g][8][nx]
+    auto seq = [=](int g, int slot) { return seqs + ((size_t)g * 5 + slot) * nxp; };
 
     RollPos cur = roll_first(f0, rs);
     roll_issue_spectra<MODE>(f0, rs, cur, stage);

@@ -1072,7 +1072,7 @@ template <class T> int StepperImpl<T>::set_fused_rows(int R) {
         return NSSTAB_ERR_INVALID_ARG;
     }
     if constexpr (kF32<T>) {
-        const int sm = 96 * kRollPoints;
+        const int sm = (int)roll_smem(kRollPoints);
         NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_RHS_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
         NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_RHS_LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
         NS_CUDA(cudaFuncSetAttribute(k_row_roll<FWD_PEN_NL>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
@@ -1095,7 +1095,7 @@ int StepperImpl<T>::launch_roll(bool pen, cudaStream_t st, bool linear, bool sfd
         Fields<T> fl = f_;
         if (act_override_) fl.active = act_override_;
         const int blocks = std::min(r.nunits, 152);
-        const size_t smem = (size_t)96 * r.G * nx_;
+        const size_t smem = roll_smem(r.G * nx_) ;
         if (!pen) {
             if (linear) k_row_roll<FWD_RHS_LIN><<<blocks, kRollThreads, smem, st>>>(fl, r, false);
             else k_row_roll<FWD_RHS_NL><<<blocks, kRollThreads, smem, st>>>(fl, r, false);
