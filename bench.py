@@ -618,7 +618,7 @@ def run_native(args, rank: int, world: int):
     if rank != 0:
         return
     clocks = clk.summary()
-    per_step_launches = 1 + 6 * nsteps + 8
+    per_step_launches = 3 + 6 * nsteps + 8   # gather, x-transform, steps, scatter; CGS2: 3 dot+reduce, 2 updates
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * el64 / args.steps, "higher_is_better": True,
