@@ -780,11 +780,15 @@ def hbm_roofline(st, v, pts: int, nsteps: int = 4):
     peak = peaks().get("hbm_gbs")
     achieved = ALG_BYTES_FP32_LIN * pts / step_s / 1e9
     dom = max(ms, key=ms.get)
-    tr = load_traffic("fp32_step_2048x1024_b128_bytes_per_pt")
+    # DRAM bytes per grid point of one whole step, from the ncu capture of 8
+    # members at 2048x1024 (each its own parameter set; here 8 members share
+    # each set's base-derived fields, so the true figure is a little lower)
+    tr = load_traffic("fp32_step_2048x1024_bytes_per_pt")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak if peak else None,
             "traffic": None if tr is None else tr * pts,
             "traffic_bytes_per_pt": tr, "algorithmic_bytes_per_pt": ALG_BYTES_FP32_LIN,
+            "dram_gbs_at_captured_traffic": None if tr is None else tr * pts / step_s / 1e9,
             "scope": "one whole linearised step (all kernels) of 128 FP32 fields at 2048x1024",
             "ms_per_step": 1e3 * step_s, "dominant_kernel": dom,
             "kernel_ms": {k: x / nsteps for k, x in ms.items()},
