@@ -23,7 +23,7 @@ moves tensors and keeps the books):
      Jacobian products and seconds.
 
 Run as ``python -m paper_1804_03859_gb300.learned_guess [options]``; prints
-one JSON line.
+one JSON line (two with --c4).
 """
 from __future__ import annotations
 
@@ -382,11 +382,11 @@ def main(argv=None):
     build.build()
     args = parse(argv)
     res = run(args)
+    # the training-grid experiment first, then (--c4) the large solve as a
+    # second line, so a long run keeps what it has finished
+    print(json.dumps({k: v for k, v in res.items() if not k.startswith("_")}), flush=True)
     if args.c4 and "_net" in res:
-        res["c4"] = run_c4(args, res)
-    res.pop("_net", None)
-    res.pop("_scale", None)
-    print(json.dumps(res))
+        print(json.dumps({"c4": run_c4(args, res)}), flush=True)
 
 
 if __name__ == "__main__":
