@@ -312,6 +312,7 @@ def run_c4(args, learned: dict) -> dict:
         _sync()
         out[label] = {"status": rc, "residual": r, "newton_iters": it, "jacobian_products": mv,
                       "newton_seconds": time.perf_counter() - t0}
+        print(json.dumps({"c4_" + label: out[label]}), flush=True)   # each solve as it finishes
         del st, lin
         torch.cuda.empty_cache()
 
