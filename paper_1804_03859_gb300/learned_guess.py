@@ -129,7 +129,9 @@ def sample_params(n: int, seed: int, re_min: float = 40.0, re_max: float = 150.0
     return [(float(rng.uniform(re_min, re_max)), float(rng.uniform(0.8, 1.2))) for _ in range(n)]
 
 
-def run(args) -> dict:
+def run(args, keep: dict | None = None) -> dict:
+    """The experiment; `keep` (optional) receives the trained network
+    ("net") and the label scale ("scale") for a later solve."""
     import torch
 
     dt = args.dt if args.dt > 0 else 0.01 * 128 / args.nx
@@ -242,6 +244,8 @@ def run(args) -> dict:
         v = [row[key][sub] for row in out_rows if row["plain"]["ok"] and row["learned"]["ok"]]
         return float(np.mean(v)) if v else None
 
+    if keep is not None:
+        keep["net"], keep["scale"] = net, scale
     return {
         "workload": f"learned Newton start, {args.nx}x{args.ny}, Re U[{args.re_min:g},{args.re_max:g}], D U[0.8,1.2]",
         "grid": [args.nx, args.ny], "dt": dt, "T": args.T, "gmres_m": args.gmres_m, "tol": args.tol,
@@ -260,7 +264,6 @@ def run(args) -> dict:
                                             if r["learned"]["guess_rel_err"] is not None] or [np.nan])),
         "rows": out_rows,
         "total_seconds": time.perf_counter() - t_all,
-        "_net": net, "_scale": scale,
     }
 
 
@@ -329,7 +332,7 @@ def run_c4(args, learned: dict) -> dict:
     solve(q, "plain")
     out["plain"].update(start=f"SFD from rest, {args.c4_sfd_steps} steps (chi {args.chi:g}, Delta {args.Delta:g})",
                         start_seconds=t_sfd, start_residual=r0)
-    net, scale = learned["_net"], learned["_scale"]
+    net, scale = learned["net"], learned["scale"]
     x = torch.from_numpy(features(args.nx, args.ny, Re, D)[None].astype(np.float32)).cuda()
     y = torch.empty(1, args.ny, args.nx, dtype=torch.float32, device="cuda")
     _sync()
@@ -382,12 +385,13 @@ def main(argv=None):
 
     build.build()
     args = parse(argv)
-    res = run(args)
+    keep = {}
+    res = run(args, keep)
     # the training-grid experiment first, then (--c4) the large solve as a
     # second line, so a long run keeps what it has finished
-    print(json.dumps({k: v for k, v in res.items() if not k.startswith("_")}), flush=True)
-    if args.c4 and "_net" in res:
-        print(json.dumps({"c4": run_c4(args, res)}), flush=True)
+    print(json.dumps(res), flush=True)
+    if args.c4 and "net" in keep:
+        print(json.dumps({"c4": run_c4(args, keep)}), flush=True)
 
 
 if __name__ == "__main__":
