@@ -305,7 +305,10 @@ int batch_arnoldi_eigs(nsstab_stepper* st, const double* base_omegas, const doub
  *         (batch_create(cfg, S, Re, D, b, ...)); S = b = 1 is a plain stepper
  *   base_omega: device [S][ny][nx] or NULL (current bases)
  *   v0:   device [S][b][ny][nx], each set's start block (linearly independent)
- *   m:    basis size per set, 2 (nev + 1) + 2 b <= m <= 1024
+ *   m:    basis size per set, 2 (nev + 1) + 2 b <= m <= 1024; the blocked
+ *         Gram-Schmidt also needs b <= 8 and (m + b) b <= 6144 (its
+ *         coefficients of one pass held in 48 KB of shared memory), so
+ *         m <= 760 at b = 8; other values give NSSTAB_ERR_INVALID_ARG
  *   eig_re, eig_im, resid: host [S][nev+1]; eigvecs: device [S][nev+1][ny][nx]
  *   or NULL; n_eig, n_conv, n_matvec: host [S] (n_matvec counts single
  *   products, b per round).  With S = 1 these are the arrays of arnoldi_eigs.

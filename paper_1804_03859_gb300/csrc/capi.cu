@@ -263,6 +263,10 @@ int block_arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const doubl
     if (nev < 1) return bad_arg("block_arnoldi_eigs: need nev >= 1");
     if (m > 1024 || m + 2L * b >= n || m < 2 * (nev + 1) + 2 * b)
         return bad_arg("block_arnoldi_eigs: need 2 (nev + 1) + 2 b <= m <= 1024 and m + 2 b < nx*ny");
+    // blocked Gram-Schmidt: at most kMaxGsBlock columns a block, and the
+    // (m + b) x b coefficients of a pass in the default 48 KB of shared memory
+    if (b > kMaxGsBlock || (long)(m + b) * b > 6144)
+        return bad_arg("block_arnoldi_eigs: need b <= 8 and (m + b) b <= 6144 (blocked Gram-Schmidt)");
     if (max_restarts < 0) return bad_arg("block_arnoldi_eigs: max_restarts < 0");
     if (!(tol >= 0)) return bad_arg("block_arnoldi_eigs: tol < 0");
     int nsteps = 0;

@@ -207,6 +207,10 @@ def test_block_krylov_schur_rejects_bad_input():
     two_sets = nsstab.Stepper(Re=[40.0, 50.0], per_set=2, nx=32, ny=16, dt=0.02)
     with pytest.raises(ValueError):
         two_sets.block_arnoldi_eigs(None, same, m=40, nev=2, tol=1e-8, T=0.4)   # needs sets * b start vectors
+    wide = nsstab.Stepper(per_set=8, nx=64, ny=32, dt=0.02, Re=50.0)
+    eight = _dev(np.stack([inputs.gaussian_field(32, 64, seed=s) for s in range(8)]))
+    with pytest.raises(nsstab.NsstabError):
+        wide.block_arnoldi_eigs(None, eight, m=800, nev=2, tol=1e-8, T=0.4)    # (m + b) b above 6144
 
 
 def test_batched_block_krylov_schur_matches_dense_per_set(small):
