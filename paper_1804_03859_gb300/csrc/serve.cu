@@ -17,6 +17,7 @@
 #include <cstring>
 #include <exception>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -304,7 +305,14 @@ static int run_wave(const nsstab_config& base_cfg, const std::vector<const Unit*
                     int wave_index, nsstab_eig_result* results) {
     cudaStream_t s = nullptr;
     NS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
-    RaggedBase* rg = make_ragged_f32(s);
+    // released in reverse order on every exit, a host exception included:
+    // the ragged launcher (which synchronises the stream and frees the
+    // groups' memory) before its stream
+    struct StreamOwner {
+        cudaStream_t s;
+        ~StreamOwner() { cudaStreamDestroy(s); }
+    } stream_owner{s};
+    std::unique_ptr<RaggedBase> rg(make_ragged_f32(s));
     std::vector<int> order;   // job index of each member
     int rc = NSSTAB_OK;
     for (const Unit* u : wave) {
@@ -362,8 +370,6 @@ static int run_wave(const nsstab_config& base_cfg, const std::vector<const Unit*
             r.resid[e] = o.resid[e];
         }
     }
-    delete rg;   // synchronises the stream and frees the groups' memory
-    cudaStreamDestroy(s);
     return rc;
 }
 
