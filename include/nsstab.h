@@ -221,8 +221,7 @@ int arnoldi_eigs(nsstab_stepper* st, const double* base_omega, const double* v0,
  * cudaMalloc, cudaFree or other allocating call.  j > NSSTAB_NOALLOC_MAX_COLS
  * is rejected with NSSTAB_ERR_INVALID_ARG.  The first call on a device looks
  * up the array's device address (cudaGetSymbolAddress) for that device, with
- * that device current; make that first call before any stream capture.  A
- * reset of the device's primary context after that first call is not
+ * that device current.  A reset of the device's primary context after that first call is not
  * supported.  All calls on a device share the array, so calls whose GPU
  * work overlaps (other streams, other host threads) race: serialise them.
  * Nothing needs clearing between calls: each call writes every scratch
