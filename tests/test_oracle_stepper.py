@@ -98,6 +98,34 @@ def test_taylor_green_continuous_second_order():
     assert 3.5 < r1 < 4.5 and 3.5 < r2 < 4.5, errs
 
 
+@pytest.mark.parametrize("nx,ny,Lx,Ly", [(64, 32, 16.0, 8.0), (48, 64, 12.0, 4.0)])
+def test_norm_h_is_the_continuous_l2_norm_of_trigonometric_fields(nx, ny, Lx, Ly):
+    """On a periodic grid the rectangle rule integrates a trigonometric
+    polynomial below the Nyquist degree exactly: the integral of
+    sin^2(kx x) sin^2(ky y) over the box is Lx Ly / 4 and that of a constant c
+    squared is c^2 Lx Ly.  A dropped or doubled cell area (dx dy) fails."""
+    cfg = ns2d.Config(nx=nx, ny=ny, Lx=Lx, Ly=Ly)
+    X, Y, kx, ky, _ = _tg_mode(cfg, 3, 2)
+    f = np.sin(kx * X) * np.sin(ky * Y)
+    assert abs(ns2d.norm_h(f, cfg) - np.sqrt(Lx * Ly) / 2) <= 1e-13 * np.sqrt(Lx * Ly)
+    assert abs(ns2d.norm_h(np.full((ny, nx), -1.5), cfg) - 1.5 * np.sqrt(Lx * Ly)) <= 1e-13 * np.sqrt(Lx * Ly)
+    both = np.stack([f, 2 * f])                     # leading axes are batch axes
+    np.testing.assert_allclose(ns2d.norm_h(both, cfg), [np.sqrt(Lx * Ly) / 2, np.sqrt(Lx * Ly)], rtol=1e-13)
+
+
+@pytest.mark.parametrize("a,b", [(2, 1), (4, 3)])
+def test_residual_of_a_decaying_mode_is_its_discrete_decay(a, b):
+    """Eq. 32's residual of a Taylor-Green mode in the free box: advection
+    vanishes, one AB1/CN step multiplies the mode by g, so
+    r = |g - 1| ||omega||_h / dt with ||omega||_h = |lam| sqrt(Lx Ly) / 2."""
+    cfg = _free_cfg(nx=64, ny=32, Uinf=0.0, Re=30.0, dt=0.02)
+    X, Y, kx, ky, lam = _tg_mode(cfg, a, b)
+    w0 = -_lap5(np.sin(kx * X) * np.sin(ky * Y), cfg)
+    g = (1 + 0.5 * cfg.nu * cfg.dt * lam) / (1 - 0.5 * cfg.nu * cfg.dt * lam)
+    ref = abs(g - 1) * abs(lam) * np.sqrt(cfg.Lx * cfg.Ly) / 2 / cfg.dt
+    assert abs(ns2d.residual(w0, cfg) - ref) <= 1e-10 * ref
+
+
 def test_tangent_is_exact_derivative_of_quadratic_step():
     """G is quadratic in omega, so the central difference equals J v up to rounding."""
     cfg = ns2d.Config(nx=64, ny=32, dt=0.02)
