@@ -91,6 +91,32 @@ def test_serve_eigs_validates_every_job_before_any_device_call(lib, job, kw, wha
     assert ng.value == -7
 
 
+@pytest.mark.parametrize("job,kw,what", [
+    (dict(nx=30), {}, "job 1"),             # grid not a power of two
+    (dict(dt=0.03), {}, "job 1"),           # T = 2 is not a whole number of steps
+    ({}, dict(nev=40), "nev"),              # nev >= m
+    ({}, dict(precision=64), "precision 32"),   # the persistent launch runs the FP32 stepper
+])
+def test_serve_eigs_persistent_validates_before_any_device_call(lib, job, kw, what):
+    """As serve_eigs, plus the FP32-only rule; no pointer is dereferenced."""
+    good = dict(nx=32, ny=16, dt=0.02, Re=50.0, cyl_D=1.0, base=16, v0=16)
+    bad = dict(good, **job)
+    jobs = (nsstab.EigJob * 2)()
+    for i, j in enumerate((good, bad)):
+        jobs[i] = nsstab.EigJob(j["nx"], j["ny"], j["dt"], j["Re"], j["cyl_D"], j["base"], j["v0"])
+    out = (nsstab.EigJobResult * 2)()
+    nw = ctypes.c_int(-7)
+    a = dict(m=40, nev=4, precision=32)
+    a.update(kw)
+    cfg = nsstab.config_default()
+    cfg.precision = a["precision"]
+    rc = lib.serve_eigs_persistent(ctypes.byref(cfg), 2, jobs, a["m"], a["nev"], 1e-6, 1, 2.0, 0, out,
+                                   ctypes.byref(nw))
+    assert rc == -1
+    assert what in lib.nsstab_last_error().decode()
+    assert nw.value == -7
+
+
 def _match(a, b):
     return max(np.min(np.abs(b - x)) for x in a)
 
